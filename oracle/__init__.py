@@ -1,0 +1,218 @@
+"""CPU oracle for the permanent -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library
+(``paper_2510_03421_gb300``) and the library never imports it.
+
+The arithmetic lives in ``perm_oracle.c`` (plain serial C, compiled with gcc by
+:func:`build`); this module only marshals numpy arrays into it.
+
+Conventions (the paper's rectangular definition, Eq. rectangular_permanent_definition):
+
+* an ``m x n`` input with ``m > n`` is evaluated as ``per(A.T)``;
+* ``per`` of a ``0 x n`` matrix is 1 (the empty product; the paper is silent);
+* integer and boolean inputs are evaluated exactly in wrapping 128-bit integer
+  arithmetic and returned as Python ``int`` (exact when the unnormalised sum fits
+  in a signed 128-bit integer);
+* float inputs are evaluated in ``long double`` (``prec="ld"``, the reference) or
+  ``double`` (``prec="f64"``, the timed CPU baseline only); complex128 inputs in
+  the corresponding complex type.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = [os.path.join(_HERE, "perm_oracle.c"), os.path.join(_HERE, "oracle_real.inc")]
+_lib = None
+_lock = threading.Lock()
+
+MAX_N = 30
+
+
+def build(force: bool = False) -> str:
+    """Compile perm_oracle.c into liboracle.so next to this file (gcc, no GPU)."""
+    newest = max(os.path.getmtime(p) for p in _SRC)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC[0], "-lm"],
+                              cwd=_HERE)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i, i64, u64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+            for prec in ("ld", "f64"):
+                for name in ("oracle_definition", "oracle_glynn", "oracle_ryser_rect"):
+                    for c in ("", "_c"):
+                        getattr(lib, "%s%s_%s" % (name, c, prec)).argtypes = [i, i, p, i64, p]
+                for c in ("", "_c"):
+                    getattr(lib, "oracle_ryser_square%s_%s" % (c, prec)).argtypes = [i, p, i64, p]
+                    getattr(lib, "oracle_glynn_partial%s_%s" % (c, prec)).argtypes = [i, i, p, i64, u64, u64, p]
+            for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
+                getattr(lib, name).argtypes = [i, i, p, i64, p]
+            lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
+            lib.oracle_glynn_partial_i128.argtypes = [i, i, p, i64, u64, u64, p]
+            lib.oracle_subset_dp_i128.argtypes = [i, i, p, i64, p]
+            lib.oracle_subset_dp_i128.restype = i
+            lib.oracle_glynn_flips.argtypes = [i, p, i64]
+            lib.oracle_glynn_flips.restype = i
+            lib.oracle_ldbl_mant_dig.restype = i
+            _lib = lib
+    return _lib
+
+
+def ldbl_mant_dig() -> int:
+    """Mantissa bits of the C long double the oracle computes in (64 on x86-64, 113 on aarch64)."""
+    return _load().oracle_ldbl_mant_dig()
+
+
+def _kind(A: np.ndarray) -> str:
+    if A.dtype.kind in "iub":
+        return "int"
+    if A.dtype.kind == "c":
+        return "complex"
+    if A.dtype.kind == "f":
+        return "real"
+    raise TypeError("unsupported dtype %s" % A.dtype)
+
+
+def _prepare(A):
+    A = np.asarray(A)
+    if A.ndim != 2:
+        raise ValueError("expected a 2-D matrix")
+    if A.shape[0] > A.shape[1]:
+        A = A.T  # per(A) = per(A^T) for m > n
+    kind = _kind(A)
+    if kind == "int":
+        A = np.ascontiguousarray(A, dtype=np.int64)
+    elif kind == "complex":
+        A = np.ascontiguousarray(A, dtype=np.complex128)
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    if n > MAX_N:
+        raise ValueError("the oracle handles n <= %d" % MAX_N)
+    return A, kind, m, n
+
+
+def _i128(buf) -> int:
+    v = int(buf[0]) | (int(buf[1]) << 64)
+    return v - (1 << 128) if v >> 127 else v
+
+
+def _real(buf, dd):
+    return (float(buf[0]), float(buf[1])) if dd else float(buf[0]) + float(buf[1])
+
+
+def _cplx(buf, dd):
+    if dd:
+        return (float(buf[0]), float(buf[1]), float(buf[2]), float(buf[3]))
+    return complex(float(buf[0]) + float(buf[1]), float(buf[2]) + float(buf[3]))
+
+
+def _call(base: str, A, prec: str = "ld", dd: bool = False, square_only: bool = False, extra=()):
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if m == 0:
+        return 1 if kind == "int" else (1.0 if kind == "real" else 1 + 0j)
+    if square_only and m != n:
+        raise ValueError("%s needs a square matrix" % base)
+    ptr = A.ctypes.data_as(ctypes.c_void_p)
+    args = (m, ptr, n) if square_only else (m, n, ptr, n)
+    if kind == "int":
+        out = (ctypes.c_uint64 * 2)()
+        getattr(lib, "%s_i128" % base)(*args, *extra, out)
+        return _i128(out)
+    if prec not in ("ld", "f64"):
+        raise ValueError("prec must be 'ld' or 'f64'")
+    if kind == "complex":
+        out = (ctypes.c_double * 4)()
+        getattr(lib, "%s_c_%s" % (base, prec))(*args, *extra, out)
+        return _cplx(out, dd)
+    out = (ctypes.c_double * 2)()
+    getattr(lib, "%s_%s" % (base, prec))(*args, *extra, out)
+    return _real(out, dd)
+
+
+def definition(A, prec: str = "ld", dd: bool = False):
+    """Sum over m-permutations of the products (Eq. rectangular_permanent_definition). Tiny n only."""
+    return _call("oracle_definition", A, prec, dd)
+
+
+def combinatoric(A, prec: str = "ld", dd: bool = False):
+    """The combinatoric algorithm is the definition evaluated directly (cost O(m n!/(n-m)!))."""
+    return definition(A, prec, dd)
+
+
+def glynn(A, prec: str = "ld", dd: bool = False):
+    """Glynn with the rectangular padding (Eq. glynn_rectangle; appendix Glynn algorithms)."""
+    return _call("oracle_glynn", A, prec, dd)
+
+
+def glynn_partial(A, g0: int, g1: int, prec: str = "ld", dd: bool = False):
+    """Unnormalised sum of Glynn terms g0 <= g < g1 (term g uses delta from gray(g) = g ^ (g >> 1),
+    bit b <-> row n-1-b, sign (-1)^g).  Integer input returns the sum modulo 2^128 as a signed int."""
+    A_, kind, m, n = _prepare(A)
+    if not (0 <= g0 <= g1 <= (1 << (n - 1))):
+        raise ValueError("term range outside [0, 2^(n-1)]")
+    return _call("oracle_glynn_partial", A_, prec, dd, extra=(g0, g1))
+
+
+def ryser_square(A, prec: str = "ld", dd: bool = False):
+    """Square Ryser over all 2^n column subsets (Eq. ryser_square; appendix algorithm)."""
+    return _call("oracle_ryser_square", A, prec, dd, square_only=True)
+
+
+def ryser_rect(A, prec: str = "ld", dd: bool = False):
+    """Rectangular Ryser over column combinations with binomial weights (Eq. ryser_rectangle)."""
+    return _call("oracle_ryser_rect", A, prec, dd)
+
+
+def ryser(A, prec: str = "ld", dd: bool = False):
+    A = np.asarray(A)
+    return ryser_square(A, prec, dd) if A.shape[0] == A.shape[1] else ryser_rect(A, prec, dd)
+
+
+def subset_dp(A) -> int:
+    """Exact integer permanent by the column-subset dynamic programme (n <= 28)."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind != "int":
+        raise TypeError("subset_dp is for integer matrices")
+    if m == 0:
+        return 1
+    out = (ctypes.c_uint64 * 2)()
+    rc = lib.oracle_subset_dp_i128(m, n, A.ctypes.data_as(ctypes.c_void_p), n, out)
+    if rc != 0:
+        raise MemoryError("subset DP table unavailable for n=%d" % n)
+    return _i128(out)
+
+
+def glynn_flips(n: int) -> list:
+    """Rows flipped, step by step, by the focus-pointer generator of the Glynn algorithms."""
+    lib = _load()
+    cap = max(1, (1 << (n - 1)) - 1)
+    buf = (ctypes.c_int * cap)()
+    cnt = lib.oracle_glynn_flips(n, buf, cap)
+    return [buf[i] for i in range(cnt)]
+
+
+def digits_lost(evaluated, true, macheps: float = np.finfo(np.float64).eps) -> float:
+    """Digits of precision lost (Eq. digits_lost): log10(|eval-true|/|true|) - log10(macheps)."""
+    err = abs(evaluated - true)
+    if err == 0:
+        return -np.inf
+    return float(np.log10(err / abs(true)) - np.log10(macheps))

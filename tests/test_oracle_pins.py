@@ -1,0 +1,345 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a value the
+paper prints, a closed form, an invariant, or brute force on tiny inputs.  A
+plausible slip anywhere in the oracle (a dropped term, a wrong sign, a wrong
+Gray-code row, a transposed operand, a wrong binomial weight or normalisation)
+fails at least one of them.
+"""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_03421_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+INT_ALGOS = {
+    "definition": oracle.definition,
+    "glynn": oracle.glynn,
+    "ryser": oracle.ryser,
+    "ryser_rect": oracle.ryser_rect,
+    "subset_dp": oracle.subset_dp,
+}
+FLOAT_ALGOS = {
+    "definition": oracle.definition,
+    "glynn": oracle.glynn,
+    "ryser": oracle.ryser,
+    "ryser_rect": oracle.ryser_rect,
+}
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def _read_worked_example():
+    rows, per = [], None
+    with open(os.path.join(GOLDEN, "worked_example_3x3.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("per"):
+                per = int(line.split()[1])
+            else:
+                rows.append([int(x) for x in line.split()])
+    return np.array(rows, dtype=np.int64), per
+
+
+# ---------------------------------------------------------------- paper values
+@pytest.mark.parametrize("name", sorted(INT_ALGOS))
+def test_worked_example_int(name):
+    A, per = _read_worked_example()
+    assert INT_ALGOS[name](A) == per == 450
+
+
+@pytest.mark.parametrize("name", sorted(FLOAT_ALGOS))
+@pytest.mark.parametrize("prec", ["ld", "f64"])
+def test_worked_example_float(name, prec):
+    A, per = _read_worked_example()
+    assert FLOAT_ALGOS[name](A.astype(np.float64), prec) == float(per)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("n", range(1, 10))
+@pytest.mark.parametrize("name", sorted(INT_ALGOS))
+def test_all_ones_square_is_factorial(n, name):
+    # precision section: the all-ones permanent is n!
+    if name == "definition" and n > 8:
+        pytest.skip("definition enumerates n! leaves")
+    assert INT_ALGOS[name](np.ones((n, n), dtype=np.int64)) == math.factorial(n)
+
+
+@pytest.mark.parametrize("m,n", [(1, 5), (2, 5), (3, 7), (4, 9), (5, 6), (2, 12), (6, 11)])
+@pytest.mark.parametrize("name", sorted(INT_ALGOS))
+def test_all_ones_rect(m, n, name):
+    # precision section: the m x n all-ones permanent is n!/(n-m)!
+    if name == "definition" and math.perm(n, m) > 2_000_000:
+        pytest.skip("too many m-permutations")
+    expect = math.factorial(n) // math.factorial(n - m)
+    assert INT_ALGOS[name](np.ones((m, n), dtype=np.int64)) == expect
+    got = FLOAT_ALGOS.get(name, oracle.glynn)(np.ones((m, n)))
+    assert _rel(got, expect) < 1e-15
+
+
+@pytest.mark.parametrize("m,n", [(3, 3), (4, 7), (6, 6), (5, 12), (9, 9)])
+def test_identity_padded_with_zero_columns(m, n):
+    # precision section: the identity (extra columns zero) has permanent 1
+    A = np.zeros((m, n), dtype=np.int64)
+    A[np.arange(m), np.arange(m)] = 1
+    for name, f in INT_ALGOS.items():
+        if name == "definition" and math.perm(n, m) > 2_000_000:
+            continue
+        assert f(A) == 1, name
+    for name in ("glynn", "ryser", "ryser_rect"):
+        assert _rel(FLOAT_ALGOS[name](A.astype(float)), 1.0) < 1e-14, name
+
+
+def _derangements(n):
+    d = [1, 0]
+    for k in range(2, n + 1):
+        d.append((k - 1) * (d[-1] + d[-2]))
+    return d[n]
+
+
+@pytest.mark.parametrize("n", range(1, 10))
+def test_derangements(n):
+    # per(J - I) counts the permutations without fixed points: D_n = (n-1)(D_{n-1} + D_{n-2})
+    A = np.ones((n, n), dtype=np.int64) - np.eye(n, dtype=np.int64)
+    for name, f in INT_ALGOS.items():
+        if name == "definition" and n > 8:
+            continue
+        assert f(A) == _derangements(n), name
+
+
+@pytest.mark.parametrize("n", range(1, 14))
+def test_tridiagonal_ones_fibonacci(n):
+    # permutations with |sigma(i) - i| <= 1 are counted by the Fibonacci number F_{n+1}
+    A = np.zeros((n, n), dtype=np.int64)
+    for i in range(n):
+        for j in range(max(0, i - 1), min(n, i + 2)):
+            A[i, j] = 1
+    fib = [0, 1]
+    while len(fib) < n + 3:
+        fib.append(fib[-1] + fib[-2])
+    for name in ("glynn", "ryser", "subset_dp"):
+        assert INT_ALGOS[name](A) == fib[n + 1], name
+    assert _rel(oracle.glynn(A.astype(float)), fib[n + 1]) < 1e-15
+
+
+@pytest.mark.parametrize("n", [4, 7, 10])
+def test_triangular_is_product_of_diagonal(n):
+    g = inputs.rng(7 + n)
+    A = np.triu(g.uniform(-1, 1, (n, n)))
+    expect = float(np.prod(np.diag(A)))
+    # the sums cancel down to prod(diag); bound the rounding by 2^n terms of size <= prod_i sum_j |a_ij|
+    bound = 2.0 ** n * n * 1e-17 * float(np.prod(np.abs(A).sum(axis=1)))
+    for name in ("glynn", "ryser", "ryser_rect"):
+        assert abs(FLOAT_ALGOS[name](A) - expect) < max(bound, 1e-15 * abs(expect)), name
+    if n <= 8:
+        assert _rel(oracle.definition(A), expect) < 1e-15
+    Ai = np.triu(g.integers(-5, 6, (n, n))).astype(np.int64)
+    expect_i = int(np.prod([int(x) for x in np.diag(Ai)]))
+    for name in ("glynn", "ryser", "subset_dp"):
+        assert INT_ALGOS[name](Ai) == expect_i, name
+
+
+def _elem_sym(v, m):
+    # e_m(v) from the coefficients of prod (x - v_k) = sum (-1)^k e_k x^(n-k)
+    c = np.poly(np.asarray(v, dtype=float))
+    return (-1) ** m * c[m]
+
+
+@pytest.mark.parametrize("m,n", [(3, 3), (5, 5), (3, 8), (6, 9), (10, 10)])
+def test_rank_one_closed_form(m, n):
+    # per(u v^T) = m! * prod(u) * e_m(v)
+    g = inputs.rng(100 + 10 * m + n)
+    u = g.uniform(0.5, 1.5, m)
+    v = g.uniform(0.5, 1.5, n)
+    A = np.outer(u, v)
+    expect = math.factorial(m) * float(np.prod(u)) * _elem_sym(v, m)
+    for name in ("glynn", "ryser"):
+        assert _rel(FLOAT_ALGOS[name](A), expect) < 1e-12, name
+
+
+def _det_fraction(M):
+    M = [row[:] for row in M]
+    n = len(M)
+    det = Fraction(1)
+    for c in range(n):
+        p = next(r for r in range(c, n) if M[r][c] != 0)
+        if p != c:
+            M[c], M[p] = M[p], M[c]
+            det = -det
+        det *= M[c][c]
+        for r in range(c + 1, n):
+            f = M[r][c] / M[c][c]
+            for k in range(c, n):
+                M[r][k] -= f * M[c][k]
+    return det
+
+
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_cauchy_borchardt_exact(n):
+    # Eq. caucy_permanent: per(C) = det(C o C) / det(C) for c_ij = 1/(x_i - y_j),
+    # evaluated exactly in rationals (x, y on a dyadic grid so C rounds once to double)
+    g = inputs.rng(300 + n)
+    x = [Fraction(int(k), 64) for k in g.choice(np.arange(16, 49), n, replace=False)]
+    y = [Fraction(-int(k), 64) for k in g.choice(np.arange(16, 49), n, replace=False)]
+    C = [[1 / (xi - yj) for yj in y] for xi in x]
+    CC = [[c * c for c in row] for row in C]
+    per_exact = _det_fraction(CC) / _det_fraction(C)
+    Af = np.array([[float(c) for c in row] for row in C])
+    # first-order effect of rounding C to double is bounded by n u per(|C|)
+    tol = 4 * n * np.finfo(float).eps * oracle.glynn(np.abs(Af)) / abs(float(per_exact))
+    for name in ("glynn", "ryser", "definition"):
+        assert _rel(FLOAT_ALGOS[name](Af), float(per_exact)) < max(tol, 1e-15), name
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7])
+def test_perfect_matching_count_brute_force(n):
+    # the permanent of a 0/1 biadjacency matrix counts perfect matchings
+    for trial in range(3):
+        A = inputs.bernoulli01(n, n, 500 + 10 * n + trial, 0.6).astype(np.int64)
+        count = sum(all(A[i, s[i]] for i in range(n)) for s in itertools.permutations(range(n)))
+        for name, f in INT_ALGOS.items():
+            assert f(A) == count, name
+
+
+def test_small_closed_forms():
+    a, b, c, d = 0.3, -1.7, 2.5, 0.9
+    A = np.array([[a, b], [c, d]])
+    for name, f in FLOAT_ALGOS.items():
+        assert _rel(f(A), a * d + b * c) < 1e-15, name
+    row = np.array([[0.5, -2.0, 3.25, 1.0]])
+    for name, f in FLOAT_ALGOS.items():
+        assert _rel(f(row), row.sum()) < 1e-15, name
+    assert oracle.glynn(np.array([[4.0]])) == 4.0
+    assert oracle.glynn(np.zeros((0, 3))) == 1.0
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("m,n", [(5, 5), (4, 7), (7, 7)])
+def test_row_column_permutation_and_transpose(m, n):
+    g = inputs.rng(40 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    ref = oracle.glynn(A)
+    for _ in range(3):
+        P = A[g.permutation(m)][:, g.permutation(n)]
+        assert _rel(oracle.glynn(P), ref) < 1e-14
+        assert _rel(oracle.ryser(P), ref) < 1e-14
+    assert _rel(oracle.glynn(A.T), ref) < 1e-14  # m > n evaluated as per(A^T)
+    assert _rel(oracle.ryser_rect(np.ascontiguousarray(A.T)), ref) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(5, 5), (4, 8)])
+def test_multilinear_in_a_row_and_scaling(m, n):
+    g = inputs.rng(60 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    x, y = g.uniform(-1, 1, n), g.uniform(-1, 1, n)
+    al, be = 0.7, -1.3
+    for f in (oracle.glynn, oracle.ryser):
+        Ax, Ay, Am = A.copy(), A.copy(), A.copy()
+        Ax[2], Ay[2], Am[2] = x, y, al * x + be * y
+        lhs, rhs = f(Am), al * f(Ax) + be * f(Ay)
+        assert abs(lhs - rhs) < 1e-13 * (abs(al * f(Ax)) + abs(be * f(Ay)) + 1e-300)
+        assert _rel(f(2.5 * A), 2.5 ** m * f(A)) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(5, 5), (4, 7)])
+def test_laplace_expansion_first_row(m, n):
+    # per(A) = sum_j a_0j per(A with row 0 and column j removed)
+    g = inputs.rng(80 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    rhs = sum(A[0, j] * oracle.glynn(np.delete(A[1:], j, axis=1)) for j in range(n))
+    assert _rel(oracle.glynn(A), rhs) < 1e-13
+    assert _rel(oracle.ryser(A), rhs) < 1e-13
+    Ai = g.integers(-9, 10, (m, n)).astype(np.int64)
+    rhs_i = sum(int(Ai[0, j]) * oracle.subset_dp(np.delete(Ai[1:], j, axis=1)) for j in range(n))
+    assert oracle.glynn(Ai) == oracle.ryser(Ai) == rhs_i
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (6, 6), (3, 7)])
+def test_complex_identities(m, n):
+    g = inputs.rng(90 + m + n)
+    A = g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))
+    ref = oracle.glynn(A)
+    for f in (oracle.ryser, oracle.definition, oracle.ryser_rect):
+        assert _rel(f(A), ref) < 1e-13
+    assert _rel(oracle.glynn(1j * A), (1j) ** m * ref) < 1e-13  # per(cA) = c^m per(A)
+    assert _rel(oracle.glynn(np.conj(A)), np.conj(ref)) < 1e-13
+    R = A.real.copy()
+    assert _rel(oracle.glynn(R + 0j), oracle.glynn(R)) < 1e-15
+
+
+# ---------------------------------------------------------------- Gray-code order
+@pytest.mark.parametrize("n", range(2, 11))
+def test_focus_pointer_is_reflected_gray_code(n):
+    # the g-th flip of the reflected binary Gray code is at bit ctz(g); the
+    # algorithm flips delta[bound - pos], i.e. row n-1-ctz(g)
+    flips = oracle.glynn_flips(n)
+    expect = [n - 1 - ((g & -g).bit_length() - 1) for g in range(1, 1 << (n - 1))]
+    assert flips == expect
+    if n == 3:
+        assert flips == [2, 1, 2]
+    if n == 4:
+        assert flips == [3, 2, 3, 1, 3, 2, 3]
+
+
+@pytest.mark.parametrize("m,n,kind", [(5, 5, "real"), (4, 7, "real"), (6, 6, "complex"), (3, 8, "complex"),
+                                      (7, 7, "int"), (4, 9, "int")])
+def test_glynn_partial_sums_the_same_terms(m, n, kind):
+    g = inputs.rng(120 + m + n)
+    if kind == "real":
+        A = g.uniform(-1, 1, (m, n))
+    elif kind == "complex":
+        A = g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))
+    else:
+        A = g.integers(-7, 8, (m, n)).astype(np.int64)
+    T = 1 << (n - 1)
+    norm = T * math.factorial(n - m)
+    full = oracle.glynn_partial(A, 0, T)
+    if kind == "int":
+        assert full % norm == 0 and full // norm == oracle.glynn(A) == oracle.subset_dp(A)
+        cuts = sorted(set([0, T] + [int(c) for c in g.integers(0, T, 5)]))
+        assert sum(oracle.glynn_partial(A, a, b) for a, b in zip(cuts, cuts[1:])) == full
+    else:
+        # the partial sum visits exactly the terms of the focus-pointer loop in the same
+        # order, so the unnormalised totals agree to the last bit of the long double
+        # (the rectangular normalisation by (n-m)! adds one long-double rounding)
+        if kind == "real":
+            F = sum(Fraction(x) for x in oracle.glynn_partial(A, 0, T, dd=True))
+            R = sum(Fraction(x) for x in oracle.glynn(A, dd=True))
+            if m == n:
+                assert F == R * norm
+            else:
+                assert abs(F / norm - R) <= Fraction(1, 2 ** 60) * abs(R)
+        assert _rel(full / norm, oracle.glynn(A)) < 1e-15
+        assert _rel(full / norm, oracle.definition(A)) < 1e-13
+
+
+def test_int_matches_long_double_and_f64():
+    g = inputs.rng(777)
+    for (m, n) in [(6, 6), (5, 9), (8, 8)]:
+        A = g.integers(-20, 21, (m, n)).astype(np.int64)
+        exact = oracle.subset_dp(A)
+        assert oracle.glynn(A) == oracle.ryser(A) == exact
+        assert abs(oracle.glynn(A.astype(float)) - exact) <= 1e-12 * abs(exact) + 1e-6
+        assert abs(oracle.ryser(A.astype(float), "f64") - exact) <= 1e-10 * abs(exact) + 1e-6
+
+
+def test_digits_lost_metric():
+    # Eq. digits_lost: log10 of the relative error minus log10 of the machine epsilon
+    eps = np.finfo(np.float64).eps
+    assert abs(oracle.digits_lost(1.0 + 1000 * eps, 1.0) - 3.0) < 1e-9
+    assert oracle.digits_lost(2.0, 2.0) == -np.inf
+
+
+def test_long_double_width_is_reported():
+    assert oracle.ldbl_mant_dig() in (53, 64, 106, 113)
