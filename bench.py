@@ -1,0 +1,274 @@
+#!/usr/bin/env python
+"""Benchmark: Glynn Gray-code terms/s for the permanent of a 36 x 36 float64
+matrix (entries i.i.d. uniform[-1, 1], fixed seed), through the C ABI.
+
+One step = one full perm_glynn call on the matrix (all 2^35 Gray-code terms:
+chunk-start rebuilds, the sweep, the reductions and the normalisation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 36] [--arith auto|fp64|fixed]
+
+Prints one JSON line (rank 0).  Under torchrun each rank computes its own copy of
+the workload on its own GPU (weak scaling, no data-path collective); ``value`` is
+the terms of all ranks divided by the slowest rank's time.  ``--impl reference``
+times the CPU oracle on the host cores on a bounded sample of the same terms.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Glynn Gray-code terms/s (n=36 FP64) & batched perms/s vs plain FP64 at stated err"
+UNIT = "terms/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=36, help="matrix order (36 is the benchmark workload)")
+    ap.add_argument("--arith", default="auto", choices=["auto", "fp64", "fixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(n: int):
+    from paper_2510_03421_gb300 import inputs
+    if n == 36:
+        A = inputs.square36_f64()
+    else:
+        A = inputs.uniform_real(n, n, inputs.SEED_BASE + 2)
+    desc = "glynn %dx%d float64 uniform[-1,1] seed %d (2^%d Gray-code terms per step)" % (
+        n, n, inputs.SEED_BASE + 2, n - 1)
+    return A, desc
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def cpu_oracle_rate(A, seconds: float, cores: int):
+    """Oracle Glynn partial sums (double, as it stands) on disjoint term ranges, one
+    per host thread; returns (terms/s, terms timed, wall seconds)."""
+    import oracle
+    oracle.build()
+    n = A.shape[0]
+    T = 1 << (n - 1)
+    probe = 1 << 10
+    t0 = time.perf_counter()
+    oracle.glynn_partial(A, 0, probe, prec="f64")
+    per_term = (time.perf_counter() - t0) / probe
+    per_thread = max(probe, int(seconds / per_term))
+    per_thread = min(per_thread, T // cores)
+    starts = [(T // cores) * k for k in range(cores)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda s: oracle.glynn_partial(A, s, s + per_thread, prec="f64"), starts))
+    wall = time.perf_counter() - t0
+    terms = per_thread * cores
+    return terms / wall, terms, wall
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r[1:5]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    A, desc = workload(args.n)
+    cores = os.cpu_count() or 1
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, per_step / 4, cores)
+    rates, terms_total, wall_total = [], 0, 0.0
+    for _ in range(args.steps):
+        r, t, w = cpu_oracle_rate(A, per_step, cores)
+        rates.append(r)
+        terms_total += t
+        wall_total += w
+    value = terms_total / wall_total
+    sample = "%d oracle Glynn terms per step (double, O(n^2) per term as the paper's base algorithm), %d threads" % (
+        terms_total // max(1, args.steps), cores)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": args.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2510_03421_gb300 import capi
+
+    A, desc = workload(args.n)
+    n = args.n
+    terms = 1 << (n - 1)
+    arith = {"auto": capi.PERM_ARITH_AUTO, "fp64": capi.PERM_ARITH_FP64, "fixed": capi.PERM_ARITH_FIXED}[args.arith]
+    dA = torch.from_numpy(A).to(dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    err = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = capi.perm_opts(arith=arith)
+    opts_err = capi.perm_opts(arith=arith, err=err.data_ptr())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+
+    # roofline denominator: FP64 FMA issue rate measured now, on this GPU
+    dfma = capi.perm_probe_rate(capi.PROBE_DFMA, local, stream)
+    peak_flops = 2.0 * dfma
+
+    for _ in range(args.warmup):
+        capi.perm_glynn(dA, out=out, stream=stream, opts=opts)
+    capi.perm_glynn(dA, out=out, stream=stream, opts=opts_err)  # result and its stated error bound
+    torch.cuda.synchronize(dev)
+    result, err_bound = float(out.item()), float(err.item())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            capi.perm_glynn(dA, out=out, stream=stream, opts=opts)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * terms * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C ABI with host (pinned) buffers, copies inside the timed region
+    hA = torch.from_numpy(A).pin_memory()
+    hout = torch.empty(1, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        capi.perm_glynn(hA, out=hout, stream=stream, opts=opts)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * terms * args.steps / e2e_s
+
+    flops_per_term = 2 * n  # n additions, n-1 multiplications, one accumulation
+    achieved = flops_per_term * terms / (ms_per_step * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "m": n, "arith": args.arith,
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+        "result": result, "err_bound": err_bound,
+        "roofline": {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
+                     "peak_source": "measured now: 2 x DFMA issue rate (perm_probe_rate)",
+                     "flops_per_term": flops_per_term},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.nbytes), "d2h_bytes_per_step": 8},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, tt, wall = cpu_oracle_rate(A, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d Glynn terms of the same matrix (oracle in double, O(n^2) per term), "
+                                          "%.1f s wall on %d threads" % (tt, wall, cores)}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

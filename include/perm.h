@@ -1,0 +1,157 @@
+/*
+ * perm.h -- C ABI of the GB300 permanent library (libperm.so).
+ *
+ * The permanent of an m x n matrix A (m <= n) is
+ *     per(A) = sum over m-permutations sigma of {1..n} of prod_i a_{i sigma(i)}
+ * (Eq. permanent_definition and Eq. rectangular_permanent_definition of the paper;
+ * for m > n the library evaluates per(A^T), as that definition prescribes, and
+ * per of a 0 x n matrix is 1).
+ *
+ * Common argument conventions for the per-matrix entry points
+ * ------------------------------------------------------------
+ *   h        handle from perm_create (owns device workspace; one host thread at a time).
+ *   A        pointer to the matrix, row-major, element (i, j) at A[i * ld + j].
+ *            May be device memory or host memory (pageable or pinned); host input
+ *            is copied to the handle's workspace on `stream` before the launch.
+ *            The caller keeps ownership.
+ *   m, n     0 <= m, n <= 64 after the transpose rule (max(m, n) <= 64).
+ *   ld       leading dimension in elements, ld >= n (ld >= m is not needed).
+ *   dtype    perm_dtype below.  Real input is double, complex input is interleaved
+ *            (re, im) doubles (ld counted in complex elements), PERM_U8 input is
+ *            one unsigned byte per entry (0/1 matrices, any value 0..255 allowed),
+ *            PERM_I64 input is int64.
+ *   out      pointer (device or host) receiving the result:
+ *              PERM_F64  -> 1 double
+ *              PERM_C128 -> 2 doubles (re, im)
+ *              PERM_U8 / PERM_I64 -> 16-byte two's-complement int128 {low u64, high u64}
+ *            Device output is written asynchronously on `stream`; host output is
+ *            written before the call returns (the call synchronises `stream`).
+ *   stream   cudaStream_t (NULL = legacy default stream).
+ *   opts     optional tuning / accuracy options (NULL = defaults).
+ *
+ * Errors: every entry point returns a perm_status.  Argument errors are reported
+ * synchronously before any work is queued.  No entry point throws, traps, aborts
+ * or prints.
+ */
+#ifndef PERM_H_
+#define PERM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PERM_F64 = 0,  /* double */
+  PERM_C128 = 1, /* complex double, interleaved (re, im) */
+  PERM_U8 = 2,   /* uint8 entries (0/1 biadjacency matrices), exact integer result */
+  PERM_I64 = 3   /* int64 entries, exact integer result */
+} perm_dtype;
+
+typedef enum {
+  PERM_OK = 0,
+  PERM_EINVAL = 1,    /* null pointer, ld < n, unknown dtype / algorithm / option */
+  PERM_ETOOBIG = 2,   /* max(m, n) > 64, or the term count exceeds opts->max_terms */
+  PERM_EOVERFLOW = 3, /* integer input whose a-priori bound may not fit in int128 */
+  PERM_ECUDA = 4,     /* a CUDA runtime call failed */
+  PERM_ENOMEM = 5,    /* workspace allocation failed */
+  PERM_EUNSUPPORTED = 6 /* combination of dtype / algorithm / option not provided */
+} perm_status;
+
+/* Arithmetic used by the real (PERM_F64) Glynn and Ryser sweeps. */
+typedef enum {
+  PERM_ARITH_AUTO = 0,  /* planner's choice */
+  PERM_ARITH_FP64 = 1,  /* FP64 column sums updated by +-2 a_rj, FP64 products, Kahan sums */
+  PERM_ARITH_FIXED = 2  /* exact 64-bit fixed-point column sums, FP64 (or wider) products */
+} perm_arith;
+
+/* How the column sums at the start of each chunk of the Gray-code sweep are formed. */
+typedef enum {
+  PERM_START_AUTO = 0,
+  PERM_START_SCALAR = 1, /* each thread sums its own rows */
+  PERM_START_DMMA = 2    /* one +-1 x A contraction per warp on the FP64 tensor cores */
+} perm_start;
+
+typedef struct {
+  int32_t chunk_log2;   /* terms between exact re-anchoring of the column sums (0 = planner) */
+  int32_t block;        /* threads per block (0 = planner) */
+  int32_t grid;         /* blocks (0 = planner: a multiple of the SM count) */
+  int32_t arith;        /* perm_arith */
+  int32_t start;        /* perm_start */
+  int32_t exhaustive;   /* perm_auto only: time every candidate instead of the cost model */
+  uint64_t max_terms;   /* refuse sweeps longer than this (0 = 2^44 terms) */
+  double* err;          /* optional pointer (device or host, like out) receiving an a-posteriori
+                           bound on |result - per(A)| (floating dtypes; complex: bound on modulus) */
+} perm_opts;
+
+typedef struct perm_handle_s* perm_handle;
+
+/* Create a handle on CUDA device `device` (workspace is allocated lazily, never
+ * during stream capture).  Returns PERM_ECUDA if the device is unusable. */
+int perm_create(perm_handle* h, int device);
+
+/* Free the handle and its workspace.  Synchronises the device first. */
+int perm_destroy(perm_handle h);
+
+/* Glynn's formula, Eq. glynn, with the rectangular extension of Eq. glynn_filled_matrix /
+ * Eq. glynn_rectangle for m < n (n - m virtual rows of ones, result divided by (n-m)!).
+ * The 2^(n-1) sign vectors are visited in reflected Gray-code order.  All dtypes. */
+int perm_glynn(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+               void* stream, const perm_opts* opts);
+
+/* Ryser's inclusion-exclusion formula: Eq. ryser_square over all 2^n column subsets
+ * (Gray-code order) for m = n, Eq. ryser_rectangle over the column subsets of sizes
+ * 1..m with weights (-1)^(m-s) C(n-s, m-s) for m < n.  All dtypes. */
+int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+               void* stream, const perm_opts* opts);
+
+/* The combinatoric algorithm: the definition (Eq. rectangular_permanent_definition)
+ * summed over all m-permutations with shared prefix products; zero entries prune
+ * whole subtrees.  Cost O(m n!/(n-m)!) on dense input; all dtypes. */
+int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+                      void* stream, const perm_opts* opts);
+
+/* Algorithm selection in place of the paper's tuned hyperplanes (Algorithm "Optimized
+ * Algorithm Selection"): a cost model trained on this library's own timings picks the
+ * algorithm and kernel configuration; opts->exhaustive times every candidate instead. */
+int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+              void* stream, const perm_opts* opts);
+
+/* Many permanents in one call.  Matrix b (0 <= b < count) has shape M[b] x N[b],
+ * row-major with leading dimension N[b], starting at element offsets[b] of `packed`
+ * (elements of `dtype`).  packed, offsets, M, N and out may each be device or host
+ * memory; out receives `count` results laid out as for the single-matrix calls.
+ * The call buckets the matrices by size and runs them in one persistent launch per
+ * bucket, captured once into a CUDA graph and replayed for the same size signature. */
+int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                 int64_t count, int dtype, void* out, void* stream, const perm_opts* opts);
+
+/* Unnormalised partial Glynn sum over the terms g_begin <= g < g_end of Eq. glynn_rectangle:
+ *     sum_g (-1)^g prod_j ( sum_{i<m} delta_i(g) a_ij + sum_{i>=m} delta_i(g) ),
+ * where delta_i(g) = -1 if bit (n-1-i) of gray(g) = g ^ (g >> 1) is set, else +1,
+ * 0 <= g_begin <= g_end <= 2^(n-1) (m <= n required; no transpose).
+ * `partial` receives, for PERM_F64, a double-double (hi, lo); for PERM_C128,
+ * (re_hi, re_lo, im_hi, im_lo); for integer dtypes the int128 sum modulo 2^128.
+ * Ranges are the unit of resumption and of sharding across devices. */
+int perm_glynn_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype,
+                       uint64_t g_begin, uint64_t g_end, void* partial, void* stream, const perm_opts* opts);
+
+/* Device-detected status since the last call of this function on handle h:
+ * PERM_EOVERFLOW if an integer call whose result went to device memory could not
+ * be guaranteed exact (its a-priori bound reached 2^126.5; the value written is
+ * still the sum modulo 2^128), else PERM_OK.  Synchronises `stream`, then clears
+ * the status.  Integer calls with a host `out` report PERM_EOVERFLOW directly. */
+int perm_device_status(perm_handle h, void* stream, int* status);
+
+/* Human-readable text of a perm_status (static storage). */
+const char* perm_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int perm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_H_ */

@@ -33,7 +33,7 @@ _SRC = [os.path.join(_HERE, "perm_oracle.c"), os.path.join(_HERE, "oracle_real.i
 _lib = None
 _lock = threading.Lock()
 
-MAX_N = 30
+MAX_N = 64
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +61,7 @@ def _load():
                 for c in ("", "_c"):
                     getattr(lib, "oracle_ryser_square%s_%s" % (c, prec)).argtypes = [i, p, i64, p]
                     getattr(lib, "oracle_glynn_partial%s_%s" % (c, prec)).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_glynn_partial_abs_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
             for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
             lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
@@ -104,7 +105,7 @@ def _prepare(A):
         A = np.ascontiguousarray(A, dtype=np.float64)
     m, n = A.shape
     if n > MAX_N:
-        raise ValueError("the oracle handles n <= %d" % MAX_N)
+        raise ValueError("the oracle handles n <= %d (full sums are only practical for small n)" % MAX_N)
     return A, kind, m, n
 
 
@@ -169,6 +170,20 @@ def glynn_partial(A, g0: int, g1: int, prec: str = "ld", dd: bool = False):
     if not (0 <= g0 <= g1 <= (1 << (n - 1))):
         raise ValueError("term range outside [0, 2^(n-1)]")
     return _call("oracle_glynn_partial", A_, prec, dd, extra=(g0, g1))
+
+
+def glynn_partial_abs(A, g0: int, g1: int, prec: str = "ld") -> float:
+    """Sum of |term| over the Glynn terms g0 <= g < g1 (real input): the scale of the
+    rounding error of any evaluation of that partial sum."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind != "real":
+        raise TypeError("glynn_partial_abs takes a real matrix")
+    if not (0 <= g0 <= g1 <= (1 << (n - 1))):
+        raise ValueError("term range outside [0, 2^(n-1)]")
+    out = (ctypes.c_double * 2)()
+    getattr(lib, "oracle_glynn_partial_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
+    return float(out[0]) + float(out[1])
 
 
 def ryser_square(A, prec: str = "ld", dd: bool = False):

@@ -17,7 +17,8 @@
  *          result is exact whenever the unnormalised sum fits in a signed
  *          128-bit integer (wrap-around is exact modulo 2^128).
  *
- * Every function requires 0 <= m <= n <= 30 (n <= 28 for the subset DP); the
+ * Every function requires 0 <= m <= n <= 64 (n <= 28 for the subset DP; the full
+ * sums are only practical for small n, the partial sums take any n); the
  * Python wrapper applies per(A) = per(A^T) for m > n and per(0 x n) = 1.
  *
  * Parity pins (tests/test_oracle_*.py): the worked 3x3 example of the usage

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of ``libperm.so`` (declared in ``include/perm.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The functions keep the C names (``perm_glynn``, ``perm_ryser``,
+``perm_combinatoric``, ``perm_auto``, ``perm_batched``, ``perm_glynn_partial``)
+and accept torch tensors (CUDA or CPU) or numpy arrays; CPU / numpy buffers are
+passed as host pointers and the library copies them itself.  If the shared
+library has not been built this module raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libperm.so")
+
+PERM_F64, PERM_C128, PERM_U8, PERM_I64 = 0, 1, 2, 3
+PERM_OK, PERM_EINVAL, PERM_ETOOBIG, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EUNSUPPORTED = range(7)
+PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED = 0, 1, 2
+PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
+
+EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
+           "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate")
+PROBE_DFMA, PROBE_DMMA, PROBE_IMAD, PROBE_IADD, PROBE_FFMA = range(5)
+
+
+class PermError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (where, status_string(status), status))
+
+
+class perm_opts(ctypes.Structure):
+    _fields_ = [("chunk_log2", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("arith", ctypes.c_int32), ("start", ctypes.c_int32), ("exhaustive", ctypes.c_int32),
+                ("max_terms", ctypes.c_uint64), ("err", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+_handles: dict = {}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libperm.so is not built (run __graft_entry__.build() or "
+                                   "python -m paper_2510_03421_gb300._build); no CPU fallback exists")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+            L.perm_create.argtypes = [ctypes.POINTER(vp), i32]
+            L.perm_destroy.argtypes = [vp]
+            for name in ("perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto"):
+                getattr(L, name).argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_glynn_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_probe_rate.argtypes = [i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+            L.perm_status_string.argtypes = [i32]
+            L.perm_status_string.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name != "perm_status_string":
+                    getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().perm_status_string(status).decode()
+
+
+def handle(device: int = 0):
+    with _lock:
+        h = _handles.get(device)
+    if h is None:
+        hv = ctypes.c_void_p()
+        rc = lib().perm_create(ctypes.byref(hv), device)
+        if rc:
+            raise PermError(rc, "perm_create")
+        with _lock:
+            h = _handles.setdefault(device, hv)
+    return h
+
+
+# ----------------------------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def dtype_code(x) -> int:
+    if _is_torch(x):
+        import torch
+        table = {torch.float64: PERM_F64, torch.complex128: PERM_C128, torch.uint8: PERM_U8,
+                 torch.bool: PERM_U8, torch.int64: PERM_I64}
+        if x.dtype not in table:
+            raise TypeError("unsupported tensor dtype %s" % x.dtype)
+        return table[x.dtype]
+    kind = np.asarray(x).dtype
+    if kind == np.float64:
+        return PERM_F64
+    if kind == np.complex128:
+        return PERM_C128
+    if kind in (np.uint8, np.bool_):
+        return PERM_U8
+    if kind == np.int64:
+        return PERM_I64
+    raise TypeError("unsupported array dtype %s" % kind)
+
+
+def _matrix(A):
+    """Returns (keepalive, pointer, m, n, ld, dtype code, torch device or None)."""
+    if _is_torch(A):
+        if A.dim() != 2:
+            raise ValueError("expected a 2-D matrix")
+        if A.numel() and A.stride(1) != 1:
+            A = A.contiguous()
+        m, n = A.shape
+        ld = A.stride(0) if A.numel() else n
+        return A, A.data_ptr(), m, n, max(ld, n), dtype_code(A), (A.device if A.is_cuda else None)
+    A = np.asarray(A)
+    if A.ndim != 2:
+        raise ValueError("expected a 2-D matrix")
+    if A.dtype == np.bool_:
+        A = A.astype(np.uint8)
+    A = np.ascontiguousarray(A)
+    m, n = A.shape
+    return A, A.ctypes.data, m, n, n, dtype_code(A), None
+
+
+def _out_like(code: int, device, count: int = 1):
+    shape = (count,) if code == PERM_F64 else (count, 2)
+    if device is not None:
+        import torch
+        tdt = torch.float64 if code in (PERM_F64, PERM_C128) else torch.int64
+        return torch.empty(shape, dtype=tdt, device=device)
+    return np.empty(shape, dtype=np.float64 if code in (PERM_F64, PERM_C128) else np.int64)
+
+
+def _ptr(x) -> int:
+    return x.data_ptr() if _is_torch(x) else x.ctypes.data
+
+
+def _stream(device, stream):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    if device is not None:
+        import torch
+        return torch.cuda.current_stream(device).cuda_stream
+    return 0
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, perm_opts):
+        return ctypes.byref(opts)
+    o = perm_opts()
+    for k, v in dict(opts).items():
+        if k == "err":
+            v = _ptr(v) if v is not None else None
+        setattr(o, k, v)
+    return ctypes.byref(o)
+
+
+def _device_index(device):
+    return 0 if device is None else (device.index if device.index is not None else 0)
+
+
+def _call(name, A, out, stream, opts):
+    keep, p, m, n, ld, code, dev = _matrix(A)
+    if out is None:
+        out = _out_like(code, dev)
+    rc = getattr(lib(), name)(handle(_device_index(dev)), p, m, n, ld, code, _ptr(out), _stream(dev, stream),
+                              _opts(opts))
+    if rc:
+        raise PermError(rc, name)
+    return out
+
+
+def perm_glynn(A, out=None, stream=None, opts=None):
+    """Glynn's formula with the rectangular extension; result written into ``out``."""
+    return _call("perm_glynn", A, out, stream, opts)
+
+
+def perm_ryser(A, out=None, stream=None, opts=None):
+    """Ryser's formula (square: all subsets; rectangular: subsets of sizes 1..m)."""
+    return _call("perm_ryser", A, out, stream, opts)
+
+
+def perm_combinatoric(A, out=None, stream=None, opts=None):
+    """The definition summed over all m-permutations."""
+    return _call("perm_combinatoric", A, out, stream, opts)
+
+
+def perm_auto(A, out=None, stream=None, opts=None):
+    """Algorithm chosen by the library's cost model."""
+    return _call("perm_auto", A, out, stream, opts)
+
+
+def perm_glynn_partial(A, g_begin: int, g_end: int, out=None, stream=None, opts=None):
+    """Unnormalised Glynn sum over terms [g_begin, g_end) (double-double / int128 modulo 2^128)."""
+    keep, p, m, n, ld, code, dev = _matrix(A)
+    if out is None:
+        words = {PERM_F64: 2, PERM_C128: 4}.get(code, 2)
+        if dev is not None:
+            import torch
+            out = torch.empty(words, dtype=torch.float64 if code in (PERM_F64, PERM_C128) else torch.int64,
+                              device=dev)
+        else:
+            out = np.empty(words, dtype=np.float64 if code in (PERM_F64, PERM_C128) else np.int64)
+    rc = lib().perm_glynn_partial(handle(_device_index(dev)), p, m, n, ld, code, g_begin, g_end, _ptr(out),
+                                  _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_glynn_partial")
+    return out
+
+
+def perm_batched(packed, offsets, M, N, out=None, stream=None, opts=None):
+    """Permanents of many matrices; matrix b is M[b] x N[b] at packed[offsets[b]:] (row-major)."""
+    code = dtype_code(packed)
+    dev = packed.device if _is_torch(packed) and packed.is_cuda else None
+    count = len(offsets)
+    if out is None:
+        out = _out_like(code, dev, count)
+    rc = lib().perm_batched(handle(_device_index(dev)), _ptr(packed), _ptr(offsets), _ptr(M), _ptr(N), count, code,
+                            _ptr(out), _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_batched")
+    return out
+
+
+def perm_probe_rate(kind: int, device: int = 0, stream=None) -> float:
+    """Measured issue rate of one pipe (include/perm_probe.h)."""
+    r = ctypes.c_double()
+    rc = lib().perm_probe_rate(device, kind, _stream(None, stream), ctypes.byref(r))
+    if rc:
+        raise PermError(rc, "perm_probe_rate")
+    return r.value
+
+
+# ----------------------------------------------------------------------------- results
+def value(out, code: int, index: int = 0):
+    """Python value of result `index` of `out` (float, complex or exact int)."""
+    arr = out.detach().cpu().numpy() if _is_torch(out) else np.asarray(out)
+    if code == PERM_F64:
+        return float(arr.reshape(-1)[index])
+    row = arr.reshape(-1, 2)[index]
+    if code == PERM_C128:
+        return complex(float(row[0]), float(row[1]))
+    lo, hi = int(row[0]) & (2 ** 64 - 1), int(row[1]) & (2 ** 64 - 1)
+    v = lo | (hi << 64)
+    return v - (1 << 128) if v >> 127 else v
+
+
+def dd_value(out) -> float:
+    """hi + lo of a double-double partial."""
+    arr = out.detach().cpu().numpy() if _is_torch(out) else np.asarray(out)
+    arr = arr.reshape(-1)
+    return float(arr[0]) + float(arr[1])

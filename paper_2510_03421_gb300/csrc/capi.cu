@@ -1,0 +1,470 @@
+// C ABI of libperm: argument checks, the transpose rule, host/device staging,
+// the launch planner and the dispatch to the kernel families.
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+#include <new>
+
+#include "../../include/perm.h"
+#include "internal.h"
+
+struct perm_handle_s {
+  int device = 0;
+  int sms = 0;
+  void* ws = nullptr;  // device workspace
+  size_t ws_bytes = 0;
+};
+
+namespace perm {
+namespace {
+
+constexpr size_t kStageA = 64 * 64 * 16;  // largest matrix operand (64 x 64 complex)
+constexpr size_t kStageOut = 256;         // result + error staging
+constexpr size_t kWsDefault = 4u << 20;
+constexpr uint64_t kDefaultMaxTerms = 1ull << 44;
+
+size_t elem_size(int dtype) {
+  switch (dtype) {
+    case PERM_F64: return 8;
+    case PERM_C128: return 16;
+    case PERM_U8: return 1;
+    case PERM_I64: return 8;
+    default: return 0;
+  }
+}
+
+size_t out_size(int dtype) { return dtype == PERM_F64 ? 8 : 16; }
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Grow the device workspace (never while `stream` is being captured into a graph).
+int ensure_ws(perm_handle h, size_t bytes, cudaStream_t stream) {
+  if (h->ws_bytes >= bytes) return PERM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  if (h->ws) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return PERM_ECUDA;
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  size_t want = bytes < kWsDefault ? kWsDefault : bytes;
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  h->ws_bytes = want;
+  // staging area and the device status word start at zero
+  if (cudaMemset(h->ws, 0, kStageA + kStageOut * 16) != cudaSuccess) return PERM_ECUDA;
+  return PERM_OK;
+}
+
+// Everything one single-matrix call needs after validation.
+struct Call {
+  perm_handle h;
+  cudaStream_t stream;
+  int dtype;
+  int m, n;         // after the transpose rule: m <= n
+  int64_t rs, cs;   // strides of the m x n operand
+  const void* dA;   // device pointer of the operand
+  void* dOut;       // device destination of the result
+  double* dErr;     // device destination of the error bound (or null)
+  void* hOut;       // host destination (or null)
+  double* hErr;     // host destination of the error bound (or null)
+  perm_opts o;
+};
+
+// Validate, apply per(A) = per(A^T) for m > n, stage host operands.
+int prepare(Call& c, perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+            void* stream, const perm_opts* opts, bool allow_transpose) {
+  if (!h || !out) return PERM_EINVAL;
+  size_t es = elem_size(dtype);
+  if (es == 0) return PERM_EINVAL;
+  if (m < 0 || n < 0 || ld < n) return PERM_EINVAL;
+  if (m > 64 || n > 64) return PERM_ETOOBIG;
+  if (m > 0 && n > 0 && !A) return PERM_EINVAL;
+  c.h = h;
+  c.stream = static_cast<cudaStream_t>(stream);
+  c.dtype = dtype;
+  c.o = opts ? *opts : perm_opts{};
+  if (c.o.arith < 0 || c.o.arith > 2 || c.o.start < 0 || c.o.start > 2 || c.o.chunk_log2 < 0 ||
+      c.o.chunk_log2 > 62 || c.o.block < 0 || c.o.block > 1024 || (c.o.block % 32) != 0 || c.o.grid < 0)
+    return PERM_EINVAL;
+  if (m > n) {
+    if (!allow_transpose) return PERM_EINVAL;
+    c.m = (int)n;
+    c.n = (int)m;
+    c.rs = 1;
+    c.cs = ld;
+  } else {
+    c.m = (int)m;
+    c.n = (int)n;
+    c.rs = ld;
+    c.cs = 1;
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  int rc = ensure_ws(h, kWsDefault, c.stream);
+  if (rc) return rc;
+  char* ws = static_cast<char*>(h->ws);
+  // operand
+  c.dA = A;
+  if (m > 0 && n > 0 && !on_device(A)) {
+    if (cudaMemcpy2DAsync(ws, (size_t)n * es, A, (size_t)ld * es, (size_t)n * es, (size_t)m, cudaMemcpyHostToDevice,
+                          c.stream) != cudaSuccess)
+      return PERM_ECUDA;
+    c.dA = ws;
+    if (m > n) {
+      c.rs = 1;
+      c.cs = n;
+    } else {
+      c.rs = n;
+      c.cs = 1;
+    }
+  }
+  // result
+  c.hOut = nullptr;
+  c.dOut = out;
+  if (!on_device(out)) {
+    c.hOut = out;
+    c.dOut = ws + kStageA;
+  }
+  c.hErr = nullptr;
+  c.dErr = c.o.err;
+  if (c.o.err && !on_device(c.o.err)) {
+    c.hErr = c.o.err;
+    c.dErr = reinterpret_cast<double*>(ws + kStageA + 64);
+  }
+  return PERM_OK;
+}
+
+int finish(Call& c, size_t out_bytes) {
+  if (cudaGetLastError() != cudaSuccess) return PERM_ECUDA;
+  if (c.hOut || c.hErr) {
+    if (c.hOut && cudaMemcpyAsync(c.hOut, c.dOut, out_bytes, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+      return PERM_ECUDA;
+    if (c.hErr && cudaMemcpyAsync(c.hErr, c.dErr, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+      return PERM_ECUDA;
+    int dev_status = 0;
+    if (c.dtype == PERM_U8 || c.dtype == PERM_I64) {
+      // host result: the integer range check is reported synchronously
+      int* sw = reinterpret_cast<int*>(static_cast<char*>(c.h->ws) + kStageA + 128);
+      if (cudaMemcpyAsync(&dev_status, sw, sizeof(int), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
+        return PERM_ECUDA;
+      if (cudaStreamSynchronize(c.stream) != cudaSuccess) return PERM_ECUDA;
+      if (dev_status) {
+        cudaMemsetAsync(sw, 0, sizeof(int), c.stream);
+        cudaStreamSynchronize(c.stream);
+        return dev_status;
+      }
+    }
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return PERM_ECUDA;
+  }
+  return PERM_OK;
+}
+
+int* status_word(perm_handle h) { return reinterpret_cast<int*>(static_cast<char*>(h->ws) + kStageA + 128); }
+
+char* partials_base(perm_handle h) { return static_cast<char*>(h->ws) + kStageA + kStageOut * 16; }
+size_t partials_capacity(perm_handle h) { return h->ws_bytes - (kStageA + kStageOut * 16); }
+
+// Grid for a sweep of `terms` terms: a multiple of the SM count at full
+// occupancy, shrunk so that every thread has at least `min_per_thread` terms.
+LaunchCfg plan_grid(perm_handle h, const perm_opts& o, int block, int bps, uint64_t terms, uint64_t min_per_thread,
+                    size_t record_bytes) {
+  LaunchCfg lc;
+  lc.block = o.block ? o.block : block;
+  int grid = o.grid ? o.grid : h->sms * (bps > 0 ? bps : 1);
+  uint64_t want = (terms + (uint64_t)lc.block * min_per_thread - 1) / ((uint64_t)lc.block * min_per_thread);
+  if (!o.grid && want < (uint64_t)grid) grid = (int)(want > 0 ? want : 1);
+  size_t cap = partials_capacity(h) / record_bytes;
+  if ((size_t)grid > cap) grid = (int)cap;
+  lc.grid = grid;
+  lc.stream = nullptr;
+  return lc;
+}
+
+int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  const bool want_abs = c.dErr != nullptr;
+  const int block = 256;
+  int bps = glynn_f64_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a;
+  a.A = c.dA;
+  a.m = c.m;
+  a.n = c.n;
+  a.rs = c.rs;
+  a.cs = c.cs;
+  a.g_begin = g0;
+  a.g_end = g1;
+  a.chunk_log2 = c.o.chunk_log2 ? c.o.chunk_log2 : 14;
+  a.start_mode = c.o.start ? c.o.start : PERM_START_SCALAR;
+  a.partials = partials_base(c.h);
+  if (launch_glynn_f64(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // error bound: products (n-1 roundings), the Kahan sum (2), and the drift of the
+  // column sums over at most 2^chunk_log2 incremental updates (n columns)
+  const double u = 1.1102230246251565e-16;
+  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
+  const double coef = u * ((double)c.n + 4.0 + 2.0 * (double)c.n * L);
+  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk) {
+  SweepArgs a;
+  a.A = c.dA;
+  a.m = c.m;
+  a.n = c.n;
+  a.rs = c.rs;
+  a.cs = c.cs;
+  a.g_begin = g0;
+  a.g_end = g1;
+  a.chunk_log2 = c.o.chunk_log2 ? c.o.chunk_log2 : default_chunk;
+  a.start_mode = c.o.start ? c.o.start : PERM_START_SCALAR;
+  a.partials = partials_base(c.h);
+  return a;
+}
+
+int glynn_cplx(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.n > glynn_c128_max_n()) return PERM_ETOOBIG;
+  if (c.o.block > 128) return PERM_EINVAL;
+  const bool want_abs = c.dErr != nullptr;
+  const int block = 128;
+  int bps = glynn_c128_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kCplxRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, g0, g1, 14);
+  if (launch_glynn_c128(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  const double u = 1.1102230246251565e-16;
+  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
+  // complex products: each rounds by at most about 2 sqrt(2) u
+  const double coef = u * (3.0 * (double)c.n + 6.0 + 2.0 * (double)c.n * L);
+  if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+int glynn_integer(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  const int block = 256;
+  int bps = glynn_int_blocks_per_sm(c.n, c.dtype, c.o.block ? c.o.block : block);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kIntRecord * sizeof(unsigned long long));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, g0, g1, 62);
+  if (!raw && launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, status_word(c.h), c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  if (launch_glynn_int(a, c.dtype, lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
+                        static_cast<unsigned long long*>(c.dOut), raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+double binomial_d(int a, int b) {
+  if (b < 0 || b > a) return 0.0;
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (unsigned __int128)(a - b + i) / (unsigned __int128)i;
+  return (double)r;
+}
+
+// Ryser over the 2^n column subsets (square: Eq. ryser_square; m < n: the subset-size
+// weights of Eq. ryser_rectangle).
+int ryser_real(Call& c) {
+  if (c.n > 62) return PERM_ETOOBIG;
+  const uint64_t terms = 1ull << c.n;
+  if (terms > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
+  const bool want_abs = c.dErr != nullptr;
+  const bool weighted = c.m < c.n;
+  const int block = 256;
+  int bps = ryser_f64_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, weighted, want_abs);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, kRealRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, terms, 14);
+  SizeWeights w;
+  for (int s = 0; s <= 64; ++s) {
+    w.w[s] = 0.0;
+    if (s <= c.n && s <= c.m) w.w[s] = (((c.m - s) & 1) ? -1.0 : 1.0) * binomial_d(c.n - s, c.m - s);
+  }
+  if (launch_ryser_f64(a, w, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  const double u = 1.1102230246251565e-16;
+  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
+  const double coef = u * ((double)c.m + 5.0 + 2.0 * (double)c.m * L);
+  const double sign = (!weighted && (c.n & 1)) ? -1.0 : 1.0;
+  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef, static_cast<double*>(c.dOut),
+                         c.dErr, false, c.stream, sign) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDefaultMaxTerms; }
+
+}  // namespace
+}  // namespace perm
+
+using namespace perm;
+
+extern "C" {
+
+int perm_version(void) { return 100; }
+
+const char* perm_status_string(int s) {
+  switch (s) {
+    case PERM_OK: return "ok";
+    case PERM_EINVAL: return "invalid argument";
+    case PERM_ETOOBIG: return "problem too large (max(m, n) > 64 or more terms than max_terms)";
+    case PERM_EOVERFLOW: return "integer result may not fit in int128";
+    case PERM_ECUDA: return "CUDA runtime error";
+    case PERM_ENOMEM: return "workspace allocation failed";
+    case PERM_EUNSUPPORTED: return "unsupported combination of dtype, algorithm and options";
+    default: return "unknown status";
+  }
+}
+
+int perm_create(perm_handle* out, int device) {
+  if (!out) return PERM_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return PERM_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return PERM_ECUDA;
+  perm_handle h = new (std::nothrow) perm_handle_s;
+  if (!h) return PERM_ENOMEM;
+  h->device = device;
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete h;
+    return PERM_ECUDA;
+  }
+  int rc = ensure_ws(h, kWsDefault, nullptr);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+
+  *out = h;
+  return PERM_OK;
+}
+
+int perm_destroy(perm_handle h) {
+  if (!h) return PERM_EINVAL;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  delete h;
+  return PERM_OK;
+}
+
+int perm_device_status(perm_handle h, void* stream, int* status) {
+  if (!h || !status) return PERM_EINVAL;
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, status_word(h), sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PERM_ECUDA;
+  if (cudaMemsetAsync(status_word(h), 0, sizeof(int), s) != cudaSuccess) return PERM_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  *status = v;
+  return PERM_OK;
+}
+
+int perm_glynn(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
+               const perm_opts* opts) {
+  Call c;
+  int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
+  if (rc) return rc;
+  if (c.m == 0) {
+    if (launch_write_one(dtype, c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+    return finish(c, out_size(dtype));
+  }
+  const uint64_t terms = 1ull << (c.n - 1);
+  if (terms > max_terms(c.o)) return PERM_ETOOBIG;
+  switch (dtype) {
+    case PERM_F64: rc = glynn_real(c, false, 0, terms); break;
+    case PERM_C128: rc = glynn_cplx(c, false, 0, terms); break;
+    default: rc = glynn_integer(c, false, 0, terms); break;
+  }
+  if (rc) return rc;
+  return finish(c, out_size(dtype));
+}
+
+int perm_glynn_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, uint64_t g_begin,
+                       uint64_t g_end, void* partial, void* stream, const perm_opts* opts) {
+  Call c;
+  if (m > n || m < 1) return PERM_EINVAL;
+  int rc = prepare(c, h, A, m, n, ld, dtype, partial, stream, opts, false);
+  if (rc) return rc;
+  const uint64_t terms = 1ull << (c.n - 1);
+  if (g_begin > g_end || g_end > terms) return PERM_EINVAL;
+  if (g_end - g_begin > max_terms(c.o)) return PERM_ETOOBIG;
+  size_t bytes = 0;
+  switch (dtype) {
+    case PERM_F64:
+      rc = glynn_real(c, true, g_begin, g_end);
+      bytes = 16;
+      break;
+    case PERM_C128:
+      rc = glynn_cplx(c, true, g_begin, g_end);
+      bytes = 32;
+      break;
+    default:
+      rc = glynn_integer(c, true, g_begin, g_end);
+      bytes = 16;
+      break;
+  }
+  if (rc) return rc;
+  return finish(c, bytes);
+}
+
+int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
+               const perm_opts* opts) {
+  Call c;
+  int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
+  if (rc) return rc;
+  if (c.m == 0) {
+    if (launch_write_one(dtype, c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+    return finish(c, out_size(dtype));
+  }
+  switch (dtype) {
+    case PERM_F64: rc = ryser_real(c); break;
+    default: return PERM_EUNSUPPORTED;
+  }
+  if (rc) return rc;
+  return finish(c, out_size(dtype));
+}
+
+int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
+                      void* stream, const perm_opts* opts) {
+  Call c;
+  int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
+  if (rc) return rc;
+  return PERM_EUNSUPPORTED;
+}
+
+int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
+              const perm_opts* opts) {
+  return perm_glynn(h, A, m, n, ld, dtype, out, stream, opts);
+}
+
+int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                 int64_t count, int dtype, void* out, void* stream, const perm_opts* opts) {
+  (void)h; (void)packed; (void)offsets; (void)M; (void)N; (void)count; (void)dtype; (void)out; (void)stream;
+  (void)opts;
+  return PERM_EUNSUPPORTED;
+}
+
+}  // extern "C"

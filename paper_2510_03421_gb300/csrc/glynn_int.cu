@@ -1,0 +1,202 @@
+// Glynn's formula (Eq. glynn, Eq. glynn_rectangle) for integer input (uint8 0/1
+// matrices or int64), exact: column sums are int64 and stay exact under the +-2 a'_rj
+// updates (so no periodic rebuild is needed beyond the start of each thread's
+// slice), products and the signed sum are taken modulo 2^128 in unsigned 128-bit
+// integers.  Wrap-around is exact modulo 2^128, so the final sum equals
+// 2^(n-1) (n-m)! per(A) whenever that value fits in a signed 128-bit integer; the
+// a-priori bound kernel below flags inputs for which that is not guaranteed.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace perm {
+namespace {
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int off) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  lo = __shfl_down_sync(0xffffffffu, lo, off);
+  hi = __shfl_down_sync(0xffffffffu, hi, off);
+  return ((u128)hi << 64) | lo;
+}
+
+// P * s modulo 2^128 for a signed 64-bit s.
+__device__ __forceinline__ u128 mul_s64(u128 P, long long s) { return P * (u128)(__int128)s; }
+
+template <typename T>
+__device__ __forceinline__ long long load_int(const void* A, int64_t e) {
+  return (long long)static_cast<const T*>(A)[e];
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(256) glynn_int_kernel(SweepArgs a) {
+  extern __shared__ long long smem_i[];
+  __shared__ u128 scratch[32];
+  const int n = a.n, m = a.m;
+  long long* sP = smem_i;          // +2 a'_ij
+  long long* sM = smem_i + n * N;  // -2 a'_ij
+  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    long long v = 0;
+    if (j < n) v = (i < m) ? load_int<T>(a.A, i * a.rs + j * a.cs) : 1;
+    sP[idx] = 2 * v;
+    sM[idx] = -2 * v;
+  }
+  __syncthreads();
+
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t g, len;
+  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+
+  u128 acc = 0;
+  long long S[N];
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = 0;
+      for (int i = 0; i < n; ++i) {
+        const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + i * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[j] += row[j];
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = (j < n) ? S[j] / 2 : 1;
+    } else {
+      const int b = ctz64(g);
+      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] += row[j];
+    }
+    u128 P = (u128)(__int128)S[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) P = mul_s64(P, S[j]);
+    if (g & 1u) acc -= P; else acc += P;
+  }
+
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += shfl_down_u128(acc, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) scratch[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    u128 x = (lane < nw) ? scratch[lane] : (u128)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += shfl_down_u128(x, off);
+    if (lane == 0) {
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials) + (size_t)blockIdx.x * kIntRecord;
+      rec[0] = (unsigned long long)x;
+      rec[1] = (unsigned long long)(x >> 64);
+    }
+  }
+}
+
+template <int N>
+void* kernel_for(int dtype) {
+  return dtype == 2 ? (void*)glynn_int_kernel<N, unsigned char> : (void*)glynn_int_kernel<N, long long>;
+}
+
+void* pick(int n, int dtype) {
+  switch ((n + 3) & ~3) {
+    case 4: return kernel_for<4>(dtype);
+    case 8: return kernel_for<8>(dtype);
+    case 12: return kernel_for<12>(dtype);
+    case 16: return kernel_for<16>(dtype);
+    case 20: return kernel_for<20>(dtype);
+    case 24: return kernel_for<24>(dtype);
+    case 28: return kernel_for<28>(dtype);
+    case 32: return kernel_for<32>(dtype);
+    case 36: return kernel_for<36>(dtype);
+    case 40: return kernel_for<40>(dtype);
+    case 44: return kernel_for<44>(dtype);
+    case 48: return kernel_for<48>(dtype);
+    case 52: return kernel_for<52>(dtype);
+    case 56: return kernel_for<56>(dtype);
+    case 60: return kernel_for<60>(dtype);
+    case 64: return kernel_for<64>(dtype);
+    default: return nullptr;
+  }
+}
+
+size_t smem_bytes(int n) { return 2u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long); }
+
+// A-priori bound on |2^(n-1) (n-m)! per(A)|: log2 of 2^(n-1) (n-m)! prod_i sum_j |a_ij|
+// and, for 0/1 matrices, of 2^(n-1) times Bregman's bound prod_i (r_i!)^(1/r_i) on
+// the permanent of the padded matrix A' (pad rows have n ones).  Also guards the
+// int64 column sums.  Sets *status = PERM_EOVERFLOW (3) if exactness is not assured.
+__global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double ln2 = 0.69314718055994530942;
+  double lrow = 0.0, lbreg = 0.0;
+  bool binary = true, zero_row = false, col_overflow = false;
+  for (int i = 0; i < m; ++i) {
+    double rsum = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const int64_t e = i * rs + j * cs;
+      double v = dtype == 2 ? (double)static_cast<const unsigned char*>(A)[e]
+                            : fabs((double)static_cast<const long long*>(A)[e]);
+      if (v > 1.0) binary = false;
+      rsum += v;
+    }
+    if (rsum == 0.0) zero_row = true;
+    else {
+      lrow += log2(rsum);
+      lbreg += lgamma(rsum + 1.0) / ln2 / rsum;
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    double csum = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const int64_t e = i * rs + j * cs;
+      csum += dtype == 2 ? (double)static_cast<const unsigned char*>(A)[e]
+                         : fabs((double)static_cast<const long long*>(A)[e]);
+    }
+    if (csum + (double)(n - m) > 2.0e18) col_overflow = true;  // 2 * 2^62 headroom for the +-2 a updates
+  }
+  if (zero_row) {
+    if (col_overflow) *status = 3;
+    return;
+  }
+  const double lfact = lgamma((double)(n - m) + 1.0) / ln2;
+  double lb = (double)(n - 1) + lfact + lrow;
+  if (binary) {
+    const double lpad = (double)(n - m) * lgamma((double)n + 1.0) / ln2 / (double)n;
+    const double lb2 = (double)(n - 1) + lbreg + lpad;
+    if (lb2 < lb) lb = lb2;
+  }
+  if (lb >= 126.5 || col_overflow) *status = 3;
+}
+
+}  // namespace
+
+int glynn_int_blocks_per_sm(int n, int dtype, int block) {
+  void* k = pick(n, dtype);
+  if (!k) return 0;
+  size_t smem = smem_bytes(n);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c) {
+  void* k = pick(a.n, dtype);
+  if (!k) return cudaErrorInvalidValue;
+  size_t smem = smem_bytes(a.n);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  SweepArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
+}
+
+cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
+                             cudaStream_t s) {
+  int_bound_kernel<<<1, 32, 0, s>>>(A, dtype, m, n, rs, cs, status);
+  return cudaGetLastError();
+}
+
+}  // namespace perm

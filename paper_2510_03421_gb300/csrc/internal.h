@@ -1,0 +1,73 @@
+// Host-side interfaces between the C ABI (capi.cu) and the kernel files.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace perm {
+
+// One Gray-code sweep over the terms [g_begin, g_end) of one matrix.
+struct SweepArgs {
+  const void* A;      // device pointer to the matrix
+  int m, n;           // m <= n <= 64 (after the transpose rule)
+  int64_t rs, cs;     // element (i, j) of the m x n operand is A[i * rs + j * cs]
+  uint64_t g_begin;   // first term
+  uint64_t g_end;     // one past the last term
+  int chunk_log2;     // column sums are rebuilt exactly at every multiple of 2^chunk_log2
+  int start_mode;     // 1 = per-thread rebuild, 2 = warp DMMA contraction
+  void* partials;     // per-block records (layout per kernel family, see below)
+};
+
+struct LaunchCfg {
+  int grid;
+  int block;
+  cudaStream_t stream;
+};
+
+// Per-block record of the real FP64 sweeps: {sum.hi, sum.lo, abssum.hi, abssum.lo}.
+constexpr int kRealRecord = 4;
+// Per-block record of the complex sweeps: {re.hi, re.lo, im.hi, im.lo, abs.hi, abs.lo}.
+constexpr int kCplxRecord = 6;
+// Per-block record of the integer sweeps: int128 as {low u64, high u64}.
+constexpr int kIntRecord = 2;
+
+// --- Glynn, real FP64 arithmetic (glynn_f64.cu)
+cudaError_t launch_glynn_f64(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
+int glynn_f64_blocks_per_sm(int n, int block, bool want_abs);
+
+// --- Glynn, complex FP64 (glynn_c128.cu); n <= glynn_c128_max_n()
+cudaError_t launch_glynn_c128(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
+int glynn_c128_blocks_per_sm(int n, int block, bool want_abs);
+int glynn_c128_max_n();
+
+// --- Glynn, exact integer (glynn_int.cu); dtype 2 = uint8, 3 = int64
+cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c);
+int glynn_int_blocks_per_sm(int n, int dtype, int block);
+// a-priori int128 range check; writes 3 (PERM_EOVERFLOW) to *status if exactness is not assured
+cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
+                             cudaStream_t s);
+
+// --- Ryser over the 2^n column subsets in Gray-code order (ryser_f64.cu)
+// w[s] = (-1)^(m-s) C(n-s, m-s) for s <= m, else 0 (used when m < n)
+struct SizeWeights {
+  double w[65];
+};
+cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, const LaunchCfg& c, bool want_abs);
+int ryser_f64_blocks_per_sm(int m, int n, int block, bool weighted, bool want_abs);
+
+// --- final reductions (reduce.cu)
+// Sum `nrec` real records in a fixed order, scale by 2^-pow2 / fact (fact = (n-m)!,
+// given as the integer whose factorial divides), write result (and error bound).
+// If `raw` is set, write the unnormalised double-double sum to out[0..1] instead.
+cudaError_t launch_finish_real(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                               double* err, bool raw, cudaStream_t s, double sign = 1.0);
+
+cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                               double* err, bool raw, cudaStream_t s);
+cudaError_t launch_finish_int(const unsigned long long* rec, int nrec, int pow2, int fact_of, unsigned long long* out,
+                              bool raw, cudaStream_t s);
+
+// Write a constant result (used for m == 0, per = 1) for a dtype code.
+cudaError_t launch_write_one(int dtype, void* out, cudaStream_t s);
+
+}  // namespace perm

@@ -1,0 +1,132 @@
+// Final reductions: fixed-order sums of the per-block partials, then the
+// normalisation of Eq. glynn_rectangle (division by 2^(n-1) and by (n-m)!) or of the
+// Ryser formulas (none, pow2 = 0 and fact_of <= 1), and the optional a-posteriori
+// error bound.  Floating-point partials are summed in double-double, integer
+// partials modulo 2^128; both orders are fixed, so results are deterministic.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace perm {
+namespace {
+
+typedef unsigned __int128 u128;
+
+__global__ void finish_real_kernel(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                                   double* err, int raw, double sign) {
+  __shared__ dd scratch[2 * 32];
+  dd v[2] = {dd{0.0, 0.0}, dd{0.0, 0.0}};
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+    v[0] = dd_add(v[0], dd{rec[kRealRecord * r], rec[kRealRecord * r + 1]});
+    v[1] = dd_add(v[1], dd{rec[kRealRecord * r + 2], rec[kRealRecord * r + 3]});
+  }
+  block_sum_dd<2>(v, scratch);
+  if (threadIdx.x != 0) return;
+  v[0].hi *= sign;  // exact
+  v[0].lo *= sign;
+  if (raw) {
+    out[0] = v[0].hi;
+    out[1] = v[0].lo;
+    if (err) err[0] = err_coef * v[1].hi;
+    return;
+  }
+  dd s = dd_ldexp(v[0], -pow2);
+  dd ab = dd_ldexp(v[1], -pow2);
+  for (int k = 2; k <= fact_of; ++k) {
+    s = dd_div_d(s, (double)k);
+    ab = dd_div_d(ab, (double)k);
+  }
+  const double r = __dadd_rn(s.hi, s.lo);
+  out[0] = r;
+  if (err) err[0] = err_coef * ab.hi + fabs(__dsub_rn(r, s.hi) - s.lo);
+}
+
+__global__ void finish_cplx_kernel(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                                   double* err, int raw) {
+  __shared__ dd scratch[3 * 32];
+  dd v[3] = {dd{0.0, 0.0}, dd{0.0, 0.0}, dd{0.0, 0.0}};
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = dd_add(v[k], dd{rec[kCplxRecord * r + 2 * k], rec[kCplxRecord * r + 2 * k + 1]});
+  }
+  block_sum_dd<3>(v, scratch);
+  if (threadIdx.x != 0) return;
+  if (raw) {
+    out[0] = v[0].hi;
+    out[1] = v[0].lo;
+    out[2] = v[1].hi;
+    out[3] = v[1].lo;
+    if (err) err[0] = err_coef * v[2].hi;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = dd_ldexp(v[k], -pow2);
+  for (int f = 2; f <= fact_of; ++f)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = dd_div_d(v[k], (double)f);
+  const double re = __dadd_rn(v[0].hi, v[0].lo), im = __dadd_rn(v[1].hi, v[1].lo);
+  out[0] = re;
+  out[1] = im;
+  if (err) err[0] = err_coef * v[2].hi + fabs(__dsub_rn(re, v[0].hi) - v[0].lo) + fabs(__dsub_rn(im, v[1].hi) - v[1].lo);
+}
+
+__global__ void finish_int_kernel(const unsigned long long* rec, int nrec, int pow2, int fact_of,
+                                  unsigned long long* out, int raw) {
+  __shared__ u128 part[256];
+  u128 acc = 0;
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x)
+    acc += ((u128)rec[kIntRecord * r + 1] << 64) | (u128)rec[kIntRecord * r];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  u128 total = 0;
+  for (int t = 0; t < (int)blockDim.x; ++t) total += part[t];
+  if (!raw) {
+    __int128 v = (__int128)total;
+    v >>= pow2;  // exact: the sum is a multiple of 2^(n-1) whenever it did not wrap
+    __int128 f = 1;
+    for (int k = 2; k <= fact_of; ++k) f *= k;
+    v /= f;
+    total = (u128)v;
+  }
+  out[0] = (unsigned long long)total;
+  out[1] = (unsigned long long)(total >> 64);
+}
+
+__global__ void write_one_kernel(int dtype, void* out) {
+  if (dtype == 0) {
+    static_cast<double*>(out)[0] = 1.0;
+  } else if (dtype == 1) {
+    static_cast<double*>(out)[0] = 1.0;
+    static_cast<double*>(out)[1] = 0.0;
+  } else {
+    static_cast<unsigned long long*>(out)[0] = 1ull;
+    static_cast<unsigned long long*>(out)[1] = 0ull;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_finish_real(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                               double* err, bool raw, cudaStream_t s, double sign) {
+  finish_real_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, err_coef, out, err, raw ? 1 : 0, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
+                               double* err, bool raw, cudaStream_t s) {
+  finish_cplx_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, err_coef, out, err, raw ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_int(const unsigned long long* rec, int nrec, int pow2, int fact_of, unsigned long long* out,
+                              bool raw, cudaStream_t s) {
+  finish_int_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, out, raw ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_one(int dtype, void* out, cudaStream_t s) {
+  write_one_kernel<<<1, 1, 0, s>>>(dtype, out);
+  return cudaGetLastError();
+}
+
+}  // namespace perm

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every entry point declared in include/perm.h; argument errors are
+reported synchronously."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_03421_gb300 import _build, capi
+    _build.build()
+    return capi.lib()
+
+
+def declared_functions():
+    import glob
+    text = "".join(open(p).read() for p in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(perm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto", "perm_batched",
+                     "perm_glynn_partial", "perm_create", "perm_destroy", "perm_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    from paper_2510_03421_gb300 import capi
+    seen = set()
+    for code in range(7):
+        s = capi.status_string(code)
+        assert s and s not in seen
+        seen.add(s)
+    assert capi.status_string(99) == "unknown status"
+    assert lib.perm_version() >= 100
+
+
+def test_null_handle_is_rejected(lib):
+    from paper_2510_03421_gb300 import capi
+    out = (ctypes.c_double * 2)()
+    a = (ctypes.c_double * 4)()
+    for name in ("perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto"):
+        rc = getattr(lib, name)(None, ctypes.addressof(a), 2, 2, 2, capi.PERM_F64, ctypes.addressof(out), None, None)
+        assert rc == capi.PERM_EINVAL, name
+    rc = lib.perm_glynn_partial(None, ctypes.addressof(a), 2, 2, 2, capi.PERM_F64, 0, 2, ctypes.addressof(out), None,
+                                None)
+    assert rc == capi.PERM_EINVAL
+    assert lib.perm_destroy(None) == capi.PERM_EINVAL
+    assert lib.perm_create(None, 0) == capi.PERM_EINVAL
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2510_03421_gb300 import capi
+    h = ctypes.c_void_p()
+    assert lib.perm_create(ctypes.byref(h), 0) == capi.PERM_ECUDA
+    assert not h.value
+
+
+def test_opts_struct_layout_matches_header():
+    from paper_2510_03421_gb300 import capi
+    # six int32, one uint64, one pointer
+    assert ctypes.sizeof(capi.perm_opts) == 6 * 4 + 8 + 8
+    assert capi.perm_opts.max_terms.offset == 24 and capi.perm_opts.err.offset == 32

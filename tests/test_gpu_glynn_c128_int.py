@@ -1,0 +1,125 @@
+"""Parity of the complex and exact-integer Glynn sweeps with the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import close, device, read_golden, run, to_dev
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+# ------------------------------------------------------------------ complex
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 14, 17])
+def test_complex_square(capi, dev, n):
+    A = inputs.complex_gaussian(n, n, 4000 + n)
+    close(run(capi, "perm_glynn", A, dev), oracle.glynn(A), A)
+
+
+@pytest.mark.parametrize("m,n", [(2, 5), (4, 9), (7, 12), (10, 15)])
+def test_complex_rectangular(capi, dev, m, n):
+    A = inputs.complex_gaussian(m, n, 4100 + m * 31 + n)
+    close(run(capi, "perm_glynn", A, dev), oracle.glynn(A), A)
+    close(run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev), oracle.glynn(A), A)
+
+
+def test_complex_real_valued_matches_real_path(capi, dev):
+    A = inputs.uniform_real(13, 13, 4201)
+    assert abs(run(capi, "perm_glynn", A + 0j, dev) - run(capi, "perm_glynn", A, dev)) <= 1e-13 * abs(oracle.glynn(A))
+
+
+def test_complex_haar_block(capi, dev):
+    A = inputs.haar_unitary_block(12, 4301)
+    close(run(capi, "perm_glynn", A, dev), oracle.glynn(A), A)
+
+
+def test_complex_partial(capi, dev):
+    import torch
+    A = inputs.complex_gaussian(10, 10, 4401)
+    out = capi.perm_glynn_partial(to_dev(A, dev), 37, 400, opts=dict(chunk_log2=4))
+    torch.cuda.synchronize(dev)
+    o = out.cpu().numpy()
+    got = complex(o[0] + o[1], o[2] + o[3])
+    ref = oracle.glynn_partial(A, 37, 400)
+    assert abs(got - ref) <= 1e-12 * max(abs(ref), 1.0) * 400
+
+
+# ------------------------------------------------------------------ integers (bit-exact)
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 10, 13, 16, 19, 22])
+def test_binary_exact(capi, dev, n):
+    A = inputs.bernoulli01(n, n, 5000 + n)
+    assert run(capi, "perm_glynn", A, dev) == oracle.subset_dp(A.astype(np.int64))
+
+
+@pytest.mark.parametrize("m,n", [(3, 6), (5, 11), (9, 14), (12, 20)])
+def test_binary_rectangular_exact(capi, dev, m, n):
+    A = inputs.bernoulli01(m, n, 5100 + m * 31 + n, 0.6)
+    assert run(capi, "perm_glynn", A, dev) == oracle.subset_dp(A.astype(np.int64))
+    assert run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev) == oracle.subset_dp(A.astype(np.int64))
+
+
+@pytest.mark.parametrize("n", [5, 12, 20, 26])
+def test_all_ones_factorial_exact(capi, dev, n):
+    assert run(capi, "perm_glynn", np.ones((n, n), dtype=np.uint8), dev) == math.factorial(n)
+    m = n // 2
+    assert run(capi, "perm_glynn", np.ones((m, n), dtype=np.uint8), dev) == math.factorial(n) // math.factorial(n - m)
+
+
+@pytest.mark.parametrize("n", [4, 9, 14])
+def test_int64_exact(capi, dev, n):
+    A = inputs.rng(5200 + n).integers(-50, 51, (n, n)).astype(np.int64)
+    assert run(capi, "perm_glynn", A, dev) == oracle.subset_dp(A)
+
+
+def test_int64_host_buffers_and_overflow_status(capi, dev):
+    A = inputs.rng(5301).integers(-9, 10, (8, 8)).astype(np.int64)
+    out = np.zeros(2, dtype=np.int64)
+    capi.perm_glynn(A, out=out)
+    assert capi.value(out, capi.PERM_I64) == oracle.subset_dp(A)
+    big = np.full((20, 20), 1 << 40, dtype=np.int64)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_glynn(big, out=np.zeros(2, dtype=np.int64))
+    assert e.value.status == capi.PERM_EOVERFLOW
+
+
+def test_device_overflow_status(capi, dev):
+    import ctypes
+
+    import torch
+    big = torch.full((20, 20), 1 << 40, dtype=torch.int64, device=dev)
+    capi.perm_glynn(big)
+    st = ctypes.c_int(-1)
+    assert capi.lib().perm_device_status(capi.handle(0), None, ctypes.byref(st)) == 0
+    assert st.value == capi.PERM_EOVERFLOW
+    A = torch.ones((6, 6), dtype=torch.uint8, device=dev)
+    capi.perm_glynn(A)
+    assert capi.lib().perm_device_status(capi.handle(0), None, ctypes.byref(st)) == 0
+    assert st.value == 0
+
+
+def test_int_partial_modular(capi, dev):
+    import torch
+    A = inputs.rng(5401).integers(-3, 4, (9, 12)).astype(np.int64)
+    for a, b in [(0, 2048), (5, 777), (1000, 1001)]:
+        out = capi.perm_glynn_partial(to_dev(A, dev), a, b)
+        torch.cuda.synchronize(dev)
+        assert capi.value(out, capi.PERM_I64) == oracle.glynn_partial(A, a, b)
+
+
+def test_config_square26_binary_golden(capi, dev):
+    g = read_golden("square26_01.txt")
+    A = inputs.square26_01(int(g["seed"][0]))
+    assert run(capi, "perm_glynn", A, dev) == int(g["per"][0])
