@@ -24,7 +24,7 @@ PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED = 0, 1, 2
 PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
-           "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate")
+           "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status")
 PROBE_DFMA, PROBE_DMMA, PROBE_IMAD, PROBE_IADD, PROBE_FFMA = range(5)
 
 
@@ -60,6 +60,8 @@ def lib():
                 getattr(L, name).argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
+            L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
             L.perm_probe_rate.argtypes = [i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
             L.perm_status_string.argtypes = [i32]
             L.perm_status_string.restype = ctypes.c_char_p
@@ -231,6 +233,20 @@ def perm_batched(packed, offsets, M, N, out=None, stream=None, opts=None):
                             _ptr(out), _stream(dev, stream), _opts(opts))
     if rc:
         raise PermError(rc, "perm_batched")
+    return out
+
+
+def perm_glynn_noalloc(A, out=None, stream=None, grid: int = 0):
+    """Real Glynn sweep that allocates nothing (scratch is a fixed device array in the
+    library); A and out must be CUDA tensors on the current device."""
+    keep, p, m, n, ld, code, dev = _matrix(A)
+    if code != PERM_F64 or dev is None:
+        raise TypeError("perm_glynn_noalloc takes a float64 CUDA tensor")
+    if out is None:
+        out = _out_like(code, dev)
+    rc = lib().perm_glynn_noalloc(p, m, n, ld, _ptr(out), _stream(dev, stream), grid)
+    if rc:
+        raise PermError(rc, "perm_glynn_noalloc")
     return out
 
 
