@@ -1,0 +1,387 @@
+// Host orchestration of perm_batched: size classes, the work lists, the per-handle
+// CUDA graph of the class kernels, and the launch-parameter tuner.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/perm.h"
+#include "handle.h"
+#include "internal.h"
+
+namespace perm {
+namespace {
+
+constexpr int kMaxBatchN = 32;  // padded orders 4..32
+constexpr int kClasses = 2 * (kMaxBatchN / 4);  // lane and warp kinds x 8 orders
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+uint64_t mix(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+// Device-side plan of one batched call: arrays laid out in the handle's batch workspace.
+struct Plan {
+  std::vector<int32_t> order, part_base;
+  std::vector<BatchItem> items;
+  struct Cls {
+    int npad = 0;
+    bool lane = false;
+    int first_item = 0, nitems = 0;
+    double cost = 0.0;
+    int grid = 1;  // blocks of the class kernel (set before capture)
+  };
+  std::vector<Cls> classes;
+  int64_t slots = 0;
+};
+
+// Order of matrix b after the transpose rule.
+inline int order_of(int m, int n) { return m > n ? m : n; }
+inline int rows_of(int m, int n) { return m > n ? n : m; }
+
+Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, const BatchTune& t) {
+  Plan p;
+  const int64_t count = (int64_t)M.size();
+  std::vector<std::vector<int32_t>> bucket(kClasses);
+  for (int64_t b = 0; b < count; ++b) {
+    const int n = order_of(M[b], N[b]);
+    const int npad = n <= 4 ? 4 : ((n + 3) & ~3);
+    const bool lane = n <= t.n_small && npad <= 16;
+    bucket[(lane ? 0 : kClasses / 2) + npad / 4 - 1].push_back((int32_t)b);
+  }
+  p.part_base.assign(count, 0);
+  for (int c = 0; c < kClasses; ++c) {
+    if (bucket[c].empty()) continue;
+    const bool lane = c < kClasses / 2;
+    const int npad = 4 * (c % (kClasses / 2) + 1);
+    std::vector<int32_t>& v = bucket[c];
+    // longest matrices first
+    std::stable_sort(v.begin(), v.end(), [&](int32_t x, int32_t y) {
+      return order_of(M[x], N[x]) > order_of(M[y], N[y]);
+    });
+    Plan::Cls cls;
+    cls.npad = npad;
+    cls.lane = lane;
+    cls.first_item = (int)p.items.size();
+    const int base = (int)p.order.size();
+    p.order.insert(p.order.end(), v.begin(), v.end());
+    if (lane) {
+      for (size_t i = 0; i < v.size(); i += 32) {
+        BatchItem it;
+        it.first = base + (int)i;
+        it.count = (int)std::min<size_t>(32, v.size() - i);
+        it.parts = 1;
+        it.pad = 0;
+        p.items.push_back(it);
+        const int n = order_of(M[v[i]], N[v[i]]);
+        cls.cost += (double)(1ull << (n > 0 ? n - 1 : 0)) * n;
+      }
+    } else {
+      std::vector<BatchItem> its;
+      for (size_t i = 0; i < v.size(); ++i) {
+        const int b = v[i];
+        const int n = order_of(M[b], N[b]);
+        const int m = rows_of(M[b], N[b]);
+        const uint64_t terms = (m > 0) ? (1ull << (n - 1)) : 1;
+        int parts = 1;
+        if (terms > (1ull << t.item_log2)) parts = (int)(terms >> t.item_log2);
+        p.part_base[b] = (int32_t)p.slots;
+        if (parts > 1) p.slots += parts;
+        for (int k = 0; k < parts; ++k) {
+          BatchItem it;
+          it.first = base + (int)i;
+          it.count = k;
+          it.parts = parts;
+          it.pad = 0;
+          its.push_back(it);
+        }
+        cls.cost += (double)terms * n / 32.0;
+      }
+      p.items.insert(p.items.end(), its.begin(), its.end());
+    }
+    cls.nitems = (int)p.items.size() - cls.first_item;
+    p.classes.push_back(cls);
+  }
+  // largest class first: it starts the graph's branches
+  std::stable_sort(p.classes.begin(), p.classes.end(),
+                   [](const Plan::Cls& x, const Plan::Cls& y) { return x.cost > y.cost; });
+  return p;
+}
+
+int ensure_bws(perm_handle_s* h, size_t bytes) {
+  if (h->bws_bytes >= bytes) return PERM_OK;
+  if (h->bws) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return PERM_ECUDA;
+    cudaFree(h->bws);
+    h->bws = nullptr;
+    h->bws_bytes = 0;
+  }
+  if (h->cache.valid) {
+    cudaGraphExecDestroy(h->cache.exec);
+    h->cache.valid = false;
+  }
+  size_t want = bytes + bytes / 4 + (1u << 20);
+  if (cudaMalloc(&h->bws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  h->bws_bytes = want;
+  return PERM_OK;
+}
+
+int ensure_streams(perm_handle_s* h) {
+  if (h->cap) return PERM_OK;
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return PERM_ECUDA;
+  for (int i = 0; i < 16; ++i) {
+    if (cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking) != cudaSuccess) return PERM_ECUDA;
+    if (cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming) != cudaSuccess) return PERM_ECUDA;
+  }
+  if (cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) return PERM_ECUDA;
+  return PERM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device layout of a plan inside bws (after the staged operand / result, if any).
+struct Layout {
+  size_t order, part_base, items, partials, done, counters, end;
+};
+
+Layout layout_of(const Plan& p, int64_t count, size_t start) {
+  Layout L;
+  L.order = align256(start);
+  L.part_base = align256(L.order + 4 * count);
+  L.items = align256(L.part_base + 4 * count);
+  L.partials = align256(L.items + sizeof(BatchItem) * p.items.size());
+  L.done = align256(L.partials + 32 * (size_t)std::max<int64_t>(p.slots, 1));
+  L.counters = align256(L.done + 4 * count);
+  L.end = align256(L.counters + 4 * kClasses);
+  return L;
+}
+
+// Enqueue the whole batched computation of plan p on stream s (class kernels on the
+// side streams, joined back into s).
+int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& args_base, int dtype,
+            const BatchTune& t, int64_t count, cudaStream_t s) {
+  char* base = static_cast<char*>(h->bws);
+  if (cudaMemsetAsync(base + L.done, 0, L.counters + 4 * kClasses - L.done, s) != cudaSuccess) return PERM_ECUDA;
+  if (cudaEventRecord(h->fork, s) != cudaSuccess) return PERM_ECUDA;
+  int k = 0;
+  for (const Plan::Cls& c : p.classes) {
+    cudaStream_t br = h->side[k % 16];
+    if (cudaStreamWaitEvent(br, h->fork, 0) != cudaSuccess) return PERM_ECUDA;
+    ClassWork cw;
+    cw.items = reinterpret_cast<const BatchItem*>(base + L.items) + c.first_item;
+    cw.nitems = c.nitems;
+    cw.counter = reinterpret_cast<int*>(base + L.counters) + k;
+    LaunchCfg lc;
+    lc.block = t.block;
+    lc.grid = c.grid;
+    lc.stream = br;
+    if (launch_batched_class(args_base, cw, dtype, c.npad, c.lane, lc) != cudaSuccess) return PERM_ECUDA;
+    if (cudaEventRecord(h->join[k % 16], br) != cudaSuccess) return PERM_ECUDA;
+    if (cudaStreamWaitEvent(s, h->join[k % 16], 0) != cudaSuccess) return PERM_ECUDA;
+    ++k;
+  }
+  (void)count;
+  return PERM_OK;
+}
+
+int upload_plan(perm_handle_s* h, const Plan& p, const Layout& L, int64_t count, cudaStream_t s) {
+  char* base = static_cast<char*>(h->bws);
+  if (count && cudaMemcpyAsync(base + L.order, p.order.data(), 4 * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (count && cudaMemcpyAsync(base + L.part_base, p.part_base.data(), 4 * count, cudaMemcpyHostToDevice, s) !=
+                   cudaSuccess)
+    return PERM_ECUDA;
+  if (!p.items.empty() && cudaMemcpyAsync(base + L.items, p.items.data(), sizeof(BatchItem) * p.items.size(),
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PERM_ECUDA;
+  // the host vectors are pageable: the copies above are complete when they return
+  return PERM_OK;
+}
+
+BatchArgs args_for(perm_handle_s* h, const Layout& L, const double* dpacked, const int64_t* doff, const int32_t* dM,
+                   const int32_t* dN, double* dout, int chunk_log2) {
+  char* base = static_cast<char*>(h->bws);
+  BatchArgs a;
+  a.packed = dpacked;
+  a.offsets = doff;
+  a.M = dM;
+  a.N = dN;
+  a.order = reinterpret_cast<const int32_t*>(base + L.order);
+  a.part_base = reinterpret_cast<const int32_t*>(base + L.part_base);
+  a.partials = reinterpret_cast<double*>(base + L.partials);
+  a.done = reinterpret_cast<int*>(base + L.done);
+  a.out = dout;
+  a.chunk_log2 = chunk_log2;
+  return a;
+}
+
+}  // namespace
+
+void batched_release(perm_handle_s* h) {
+  if (h->cache.valid) cudaGraphExecDestroy(h->cache.exec);
+  h->cache.valid = false;
+  if (h->bws) cudaFree(h->bws);
+  h->bws = nullptr;
+  if (h->cap) {
+    cudaStreamDestroy(h->cap);
+    for (int i = 0; i < 16; ++i) {
+      cudaStreamDestroy(h->side[i]);
+      cudaEventDestroy(h->join[i]);
+    }
+    cudaEventDestroy(h->fork);
+    h->cap = nullptr;
+  }
+}
+
+int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                int64_t count, int dtype, void* out, cudaStream_t s, const void* opts_v) {
+  const perm_opts* opts = static_cast<const perm_opts*>(opts_v);
+  if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
+  if (dtype != PERM_F64 && dtype != PERM_C128) return (dtype == PERM_U8 || dtype == PERM_I64) ? PERM_EUNSUPPORTED
+                                                                                              : PERM_EINVAL;
+  if (count == 0) return PERM_OK;
+  if (count > (1ll << 30)) return PERM_ETOOBIG;
+  const int W = dtype == PERM_C128 ? 2 : 1;
+  int rc = ensure_streams(h);
+  if (rc) return rc;
+  // sizes on the host
+  std::vector<int64_t> hoff(count);
+  std::vector<int32_t> hM(count), hN(count);
+  const bool dev_off = on_device(offsets), dev_M = on_device(M), dev_N = on_device(N);
+  if (dev_off || dev_M || dev_N) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  if (cudaMemcpy(hoff.data(), offsets, 8 * count, dev_off ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(hM.data(), M, 4 * count, dev_M ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess ||
+      cudaMemcpy(hN.data(), N, 4 * count, dev_N ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
+    return PERM_ECUDA;
+  int64_t elems = 0;
+  uint64_t hist = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    if (hM[b] < 0 || hN[b] < 0 || hoff[b] < 0) return PERM_EINVAL;
+    if (order_of(hM[b], hN[b]) > kMaxBatchN) return PERM_ETOOBIG;
+    elems = std::max<int64_t>(elems, hoff[b] + (int64_t)hM[b] * hN[b]);
+  }
+  for (int64_t b = 0; b < count; ++b) hist = mix(hist, (uint64_t)hM[b] * 131 + hN[b]);
+
+  BatchTune t = h->tune;
+  if (opts && opts->chunk_log2) t.chunk_log2 = opts->chunk_log2;
+  if (opts && opts->block) {
+    if (opts->block % 32 || opts->block > 128) return PERM_EINVAL;
+    t.block = opts->block;
+  }
+
+  // staged operands (host packed / out) live at the start of the batch workspace
+  const bool host_packed = !on_device(packed), host_out = !on_device(out);
+  const bool host_sizes = !dev_off || !dev_M || !dev_N;
+  size_t start = 0;
+  size_t packed_at = 0, out_at = 0, sizes_at = 0;
+  if (host_packed) {
+    packed_at = start;
+    start = align256(start + 8 * W * (size_t)elems);
+  }
+  if (host_out) {
+    out_at = start;
+    start = align256(start + 8 * W * (size_t)count);
+  }
+  if (host_sizes) {
+    sizes_at = start;
+    start = align256(start + 16 * (size_t)count);
+  }
+
+  Plan p = build_plan(hM, hN, t);
+  for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
+    const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+    const int warps_per_block = t.block / 32;
+    int grid = h->sms * (bps > 0 ? bps : 1);
+    const int need = (c.nitems + warps_per_block - 1) / warps_per_block;
+    if (need < grid) grid = need > 0 ? need : 1;
+    c.grid = grid;
+  }
+  Layout L = layout_of(p, count, start);
+  rc = ensure_bws(h, L.end);
+  if (rc) return rc;
+  char* base = static_cast<char*>(h->bws);
+  const double* dpacked = static_cast<const double*>(packed);
+  double* dout = static_cast<double*>(out);
+  const int64_t* doff = offsets;
+  const int32_t* dM = M;
+  const int32_t* dN = N;
+  if (host_packed) {
+    if (cudaMemcpyAsync(base + packed_at, packed, 8 * W * (size_t)elems, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PERM_ECUDA;
+    dpacked = reinterpret_cast<const double*>(base + packed_at);
+  }
+  if (host_out) dout = reinterpret_cast<double*>(base + out_at);
+  if (host_sizes) {
+    char* sz = base + sizes_at;
+    if (cudaMemcpyAsync(sz, hoff.data(), 8 * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sz + 8 * count, hM.data(), 4 * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sz + 12 * count, hN.data(), 4 * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PERM_ECUDA;
+    doff = reinterpret_cast<const int64_t*>(sz);
+    dM = reinterpret_cast<const int32_t*>(sz + 8 * count);
+    dN = reinterpret_cast<const int32_t*>(sz + 12 * count);
+  }
+
+  uint64_t key = mix(hist, (uint64_t)count);
+  key = mix(key, (uint64_t)dtype);
+  key = mix(key, (uint64_t)(uintptr_t)dpacked);
+  key = mix(key, (uint64_t)(uintptr_t)dout);
+  key = mix(key, (uint64_t)(uintptr_t)doff);
+  key = mix(key, (uint64_t)(uintptr_t)dM);
+  key = mix(key, (uint64_t)(uintptr_t)dN);
+  key = mix(key, (uint64_t)t.n_small * 1000003ull + t.item_log2 * 1009 + t.chunk_log2 * 31 + t.block);
+  key = mix(key, (uint64_t)(uintptr_t)h->bws);
+
+  BatchArgs args = args_for(h, L, dpacked, doff, dM, dN, dout, t.chunk_log2);
+  if (!(h->cache.valid && h->cache.key == key)) {
+    if (h->cache.valid) {
+      cudaGraphExecDestroy(h->cache.exec);
+      h->cache.valid = false;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+    rc = upload_plan(h, p, L, count, h->cap);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(h->cap) != cudaSuccess) return PERM_ECUDA;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PERM_ECUDA;
+    rc = enqueue(h, p, L, args, dtype, t, count, h->cap);
+    cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+    if (rc || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc ? rc : PERM_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return PERM_ECUDA;
+    h->cache.exec = exec;
+    h->cache.key = key;
+    h->cache.valid = true;
+  }
+  if (cudaGraphLaunch(h->cache.exec, s) != cudaSuccess) return PERM_ECUDA;
+  if (host_out) {
+    if (cudaMemcpyAsync(out, dout, 8 * W * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PERM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+}  // namespace perm

@@ -1,6 +1,7 @@
 // C ABI of libperm: argument checks, the transpose rule, host/device staging,
 // the launch planner and the dispatch to the kernel families.
 #include <cstdint>
+#include <cmath>
 #include <cstring>
 #include <cuda_runtime.h>
 #include <new>
@@ -8,12 +9,7 @@
 #include "../../include/perm.h"
 #include "internal.h"
 
-struct perm_handle_s {
-  int device = 0;
-  int sms = 0;
-  void* ws = nullptr;  // device workspace
-  size_t ws_bytes = 0;
-};
+#include "handle.h"
 
 namespace perm {
 namespace {
@@ -157,25 +153,28 @@ int finish(Call& c, size_t out_bytes) {
     int dev_status = 0;
     if (c.dtype == PERM_U8 || c.dtype == PERM_I64) {
       // host result: the integer range check is reported synchronously
-      int* sw = reinterpret_cast<int*>(static_cast<char*>(c.h->ws) + kStageA + 128);
+      int* sw = reinterpret_cast<int*>(static_cast<char*>(c.h->ws) + kStageA + 132);
       if (cudaMemcpyAsync(&dev_status, sw, sizeof(int), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
         return PERM_ECUDA;
       if (cudaStreamSynchronize(c.stream) != cudaSuccess) return PERM_ECUDA;
-      if (dev_status) {
-        cudaMemsetAsync(sw, 0, sizeof(int), c.stream);
-        cudaStreamSynchronize(c.stream);
-        return dev_status;
-      }
+      if (dev_status) return dev_status;
     }
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) return PERM_ECUDA;
   }
   return PERM_OK;
 }
 
+// sticky device status (calls with device output; read by perm_device_status)
 int* status_word(perm_handle h) { return reinterpret_cast<int*>(static_cast<char*>(h->ws) + kStageA + 128); }
+// status of the current call when its result goes to host memory (cleared per call)
+int* call_status_word(perm_handle h) { return reinterpret_cast<int*>(static_cast<char*>(h->ws) + kStageA + 132); }
 
-char* partials_base(perm_handle h) { return static_cast<char*>(h->ws) + kStageA + kStageOut * 16; }
-size_t partials_capacity(perm_handle h) { return h->ws_bytes - (kStageA + kStageOut * 16); }
+// workspace layout: [staged operand | result/err/status | fixed-point table | partial records]
+constexpr size_t kFxTableOffset = kStageA + kStageOut * 16;
+constexpr size_t kPartialsOffset = kFxTableOffset + ((sizeof(FxTable) + 255) / 256) * 256;
+FxTable* fx_table(perm_handle h) { return reinterpret_cast<FxTable*>(static_cast<char*>(h->ws) + kFxTableOffset); }
+char* partials_base(perm_handle h) { return static_cast<char*>(h->ws) + kPartialsOffset; }
+size_t partials_capacity(perm_handle h) { return h->ws_bytes - kPartialsOffset; }
 
 // Grid for a sweep of `terms` terms: a multiple of the SM count at full
 // occupancy, shrunk so that every thread has at least `min_per_thread` terms.
@@ -193,7 +192,7 @@ LaunchCfg plan_grid(perm_handle h, const perm_opts& o, int block, int bps, uint6
   return lc;
 }
 
-int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   const bool want_abs = c.dErr != nullptr;
   const int block = 256;
   int bps = glynn_f64_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
@@ -220,6 +219,34 @@ int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
                          static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
+}
+
+SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk);
+
+// Real Glynn on the integer pipes: exact fixed-point column sums, 64-bit-mantissa
+// products, 192-bit accumulation (glynn_fx.cu).
+int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  const bool want_abs = c.dErr != nullptr;
+  const int block = 256;
+  int bps = glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
+  lc.stream = c.stream;
+  // the 192-bit accumulator holds up to 2^40 maximal terms per thread
+  if ((g1 - g0) / ((uint64_t)lc.grid * lc.block) >= (1ull << 40)) return PERM_ETOOBIG;
+  SweepArgs a = sweep_args(c, g0, g1, 62);
+  if (launch_glynn_fx(a, fx_table(c.h), lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // products: n truncations of < 2^-62 each; quantisation of A: < 2^-62 of each column's
+  // absolute sum; both taken relative to sum |t|
+  const double coef = std::ldexp(2.0 * (double)c.n + 4.0, -62);
+  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.o.arith == PERM_ARITH_FIXED) return glynn_fixed(c, raw, g0, g1);
+  return glynn_fp64(c, raw, g0, g1);
 }
 
 SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk) {
@@ -263,8 +290,9 @@ int glynn_integer(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kIntRecord * sizeof(unsigned long long));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 62);
-  if (!raw && launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, status_word(c.h), c.stream) != cudaSuccess)
-    return PERM_ECUDA;
+  int* st = c.hOut ? call_status_word(c.h) : status_word(c.h);
+  if (c.hOut && cudaMemsetAsync(st, 0, sizeof(int), c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (!raw && launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, st, c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_glynn_int(a, c.dtype, lc) != cudaSuccess) return PERM_ECUDA;
   if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
@@ -307,6 +335,43 @@ int ryser_real(Call& c) {
                          c.dErr, false, c.stream, sign) != cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
+}
+
+// The combinatoric algorithm over all injective maps (combinatoric.cu).
+int combinatoric_run(Call& c) {
+  // dense count of injective maps n!/(n-m)! (sparse inputs are pruned, so this bounds the work)
+  long double leaves = 1.0L;
+  for (int k = 0; k < c.m; ++k) leaves *= (long double)(c.n - k);
+  const uint64_t cap = c.o.max_terms ? c.o.max_terms : (1ull << 44);
+  if (leaves > (long double)cap) return PERM_ETOOBIG;
+  const int block = 128;
+  if (c.o.block > 128) return PERM_EINVAL;
+  int bps = combinatoric_blocks_per_sm(c.m, c.n, c.dtype, c.o.block ? c.o.block : block);
+  const size_t rec = (c.dtype == PERM_F64) ? kRealRecord * 8 : (c.dtype == PERM_C128 ? kCplxRecord * 8 : kIntRecord * 8);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, ~0ull >> 1, 1, rec);
+  lc.stream = c.stream;
+  const uint64_t threads = (uint64_t)lc.grid * lc.block;
+  int depth = 0;
+  uint64_t prefixes = 1;
+  while (depth < c.m && prefixes < 8 * threads) {
+    prefixes *= (uint64_t)(c.n - depth);
+    ++depth;
+  }
+  if (!c.o.grid && prefixes < threads) lc.grid = (int)((prefixes + lc.block - 1) / lc.block);
+  SweepArgs a = sweep_args(c, 0, 0, 0);
+  if (launch_combinatoric(a, c.dtype, depth, prefixes, lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
+  cudaError_t e;
+  if (c.dtype == PERM_F64)
+    e = launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, 0.0, static_cast<double*>(c.dOut),
+                           nullptr, false, c.stream);
+  else if (c.dtype == PERM_C128)
+    e = launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, 0, 0, 0.0, static_cast<double*>(c.dOut),
+                           nullptr, false, c.stream);
+  else
+    e = launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, 0, 0,
+                          static_cast<unsigned long long*>(c.dOut), false, c.stream);
+  return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
 uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDefaultMaxTerms; }
@@ -364,6 +429,7 @@ int perm_destroy(perm_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  batched_release(h);
   delete h;
   return PERM_OK;
 }
@@ -452,7 +518,14 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
   Call c;
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
-  return PERM_EUNSUPPORTED;
+  if (c.m == 0) {
+    if (launch_write_one(dtype, c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+    return finish(c, out_size(dtype));
+  }
+  rc = combinatoric_run(c);
+  if (rc) return rc;
+  return finish(c, out_size(dtype));
 }
 
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
@@ -462,9 +535,9 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
 
 int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                  int64_t count, int dtype, void* out, void* stream, const perm_opts* opts) {
-  (void)h; (void)packed; (void)offsets; (void)M; (void)N; (void)count; (void)dtype; (void)out; (void)stream;
-  (void)opts;
-  return PERM_EUNSUPPORTED;
+  if (!h) return PERM_EINVAL;
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  return batched_run(h, packed, offsets, M, N, count, dtype, out, static_cast<cudaStream_t>(stream), opts);
 }
 
 }  // extern "C"

@@ -1,0 +1,246 @@
+// The combinatoric algorithm: the definition (Eq. rectangular_permanent_definition)
+// summed over all injective maps sigma: rows -> columns, cost O(m n!/(n-m)!).
+//
+// The maps are split by their first d rows: prefix r (0 <= r < n!/(n-d)!) is read as
+// mixed-radix digits choosing, for rows 0..d-1 in turn, the digit-th still unused
+// column.  A thread takes prefixes in a grid-stride loop; a prefix whose product is
+// zero is skipped, and below it a depth-first search visits the remaining rows with
+// a bitmask of the columns still free and of the row's nonzero entries, so zero
+// entries prune whole subtrees.  The search evaluates each subtree bottom-up
+// (value(row k) = sum over free columns c of a_kc * value(row k+1)), so rounding
+// grows with the depth of the tree, not with the number of leaves.  Prefix values are
+// combined in a Kahan sum (real, complex) or modulo 2^128 (integer).
+#include <type_traits>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace perm {
+namespace {
+
+typedef unsigned __int128 u128;
+
+struct RealF {
+  typedef double T;
+  __device__ static T zero() { return 0.0; }
+  __device__ static T one() { return 1.0; }
+  __device__ static T load(const void* A, int64_t e) { return static_cast<const double*>(A)[e]; }
+  __device__ static bool is_zero(T x) { return x == 0.0; }
+  __device__ static T mul(T a, T b) { return __dmul_rn(a, b); }
+  __device__ static T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
+  __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
+};
+
+struct CplxF {
+  typedef double2 T;
+  __device__ static T zero() { return make_double2(0.0, 0.0); }
+  __device__ static T one() { return make_double2(1.0, 0.0); }
+  __device__ static T load(const void* A, int64_t e) {
+    const double* p = static_cast<const double*>(A) + 2 * e;
+    return make_double2(p[0], p[1]);
+  }
+  __device__ static bool is_zero(T x) { return x.x == 0.0 && x.y == 0.0; }
+  __device__ static T mul(T a, T b) {
+    return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+  }
+  __device__ static T fma(T a, T b, T c) {
+    T p = mul(a, b);
+    return make_double2(__dadd_rn(p.x, c.x), __dadd_rn(p.y, c.y));
+  }
+  __device__ static T add(T a, T b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+};
+
+template <typename E>
+struct IntF {
+  typedef u128 T;
+  __device__ static T zero() { return 0; }
+  __device__ static T one() { return 1; }
+  __device__ static T load(const void* A, int64_t e) { return (u128)(__int128)(long long)static_cast<const E*>(A)[e]; }
+  __device__ static bool is_zero(T x) { return x == 0; }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T fma(T a, T b, T c) { return a * b + c; }
+  __device__ static T add(T a, T b) { return a + b; }
+};
+
+constexpr int kMaxN = 64;
+
+// Compensated accumulation of prefix values.
+__device__ __forceinline__ void kahan(double& acc, double& comp, double x) {
+  const double y = __dsub_rn(x, comp);
+  const double s = __dadd_rn(acc, y);
+  comp = __dsub_rn(__dsub_rn(s, acc), y);
+  acc = s;
+}
+
+template <class F>
+__global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes) {
+  typedef typename F::T T;
+  extern __shared__ unsigned char smem_c[];
+  __shared__ unsigned long long rowmask[kMaxN];
+  const int n = a.n, m = a.m;
+  T* sA = reinterpret_cast<T*>(smem_c);  // sA[i * n + j]
+  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    sA[idx] = F::load(a.A, i * a.rs + j * a.cs);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    unsigned long long mk = 0;
+    for (int j = 0; j < n; ++j)
+      if (!F::is_zero(sA[i * n + j])) mk |= 1ull << j;
+    rowmask[i] = mk;
+  }
+  __syncthreads();
+
+  // per-thread accumulators: Kahan pairs for floating point, u128 for integers
+  T acc = F::zero();
+  double kr = 0.0, kcr = 0.0, ki = 0.0, kci = 0.0;
+  // depth-first state (local memory)
+  unsigned long long cand[kMaxN];
+  int col[kMaxN];
+  T val[kMaxN + 1];
+
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < prefixes; r += stride) {
+    // unrank the prefix
+    uint64_t rem = r;
+    unsigned long long used = 0;
+    T pre = F::one();
+    bool zero = false;
+    for (int k = 0; k < depth; ++k) {
+      const int radix = n - k;
+      int digit = (int)(rem % (uint64_t)radix);
+      rem /= (uint64_t)radix;
+      unsigned long long freecols = ~used & ((n == 64) ? ~0ull : ((1ull << n) - 1));
+      for (int t = 0; t < digit; ++t) freecols &= freecols - 1;
+      const int c = __ffsll((long long)freecols) - 1;
+      used |= 1ull << c;
+      const T v = sA[k * n + c];
+      if (F::is_zero(v)) zero = true;
+      pre = F::mul(pre, v);
+    }
+    if (zero) continue;
+    T sub;
+    if (depth == m) {
+      sub = F::one();
+    } else {
+      // value of rows depth..m-1 over the free columns, bottom-up
+      int k = depth;
+      cand[k] = rowmask[k] & ~used;
+      val[k] = F::zero();
+      while (true) {
+        if (k == m - 1) {
+          T s = F::zero();
+          unsigned long long cm = cand[k];
+          while (cm) {
+            const int c = __ffsll((long long)cm) - 1;
+            cm &= cm - 1;
+            s = F::add(s, sA[k * n + c]);
+          }
+          val[k] = s;
+          cand[k] = 0;
+        }
+        if (cand[k] == 0) {
+          if (k == depth) break;
+          --k;  // return val[k+1] to the parent
+          used &= ~(1ull << col[k]);
+          val[k] = F::fma(sA[k * n + col[k]], val[k + 1], val[k]);
+          continue;
+        }
+        const int c = __ffsll((long long)cand[k]) - 1;
+        cand[k] &= cand[k] - 1;
+        col[k] = c;
+        used |= 1ull << c;
+        ++k;
+        cand[k] = rowmask[k] & ~used;
+        val[k] = F::zero();
+      }
+      sub = val[depth];
+    }
+    const T contrib = F::mul(pre, sub);
+    if constexpr (std::is_same_v<T, double>) {
+      kahan(kr, kcr, contrib);
+    } else if constexpr (std::is_same_v<T, double2>) {
+      kahan(kr, kcr, contrib.x);
+      kahan(ki, kci, contrib.y);
+    } else {
+      acc = F::add(acc, contrib);
+    }
+  }
+
+  // block reduction into one record per block
+  if constexpr (std::is_same_v<T, u128>) {
+    __shared__ u128 part[128];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u128 t = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) t += part[i];
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials) + (size_t)blockIdx.x * kIntRecord;
+      rec[0] = (unsigned long long)t;
+      rec[1] = (unsigned long long)(t >> 64);
+    }
+  } else {
+    __shared__ dd scratch[3 * 32];
+    dd v[3] = {two_sum(kr, -kcr), two_sum(ki, -kci), dd{0.0, 0.0}};
+    block_sum_dd<3>(v, scratch);
+    if (threadIdx.x == 0) {
+      if constexpr (std::is_same_v<T, double>) {
+        double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+        rec[0] = v[0].hi;
+        rec[1] = v[0].lo;
+        rec[2] = 0.0;
+        rec[3] = 0.0;
+      } else {
+        double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kCplxRecord;
+        rec[0] = v[0].hi;
+        rec[1] = v[0].lo;
+        rec[2] = v[1].hi;
+        rec[3] = v[1].lo;
+        rec[4] = 0.0;
+        rec[5] = 0.0;
+      }
+    }
+  }
+}
+
+void* pick(int dtype) {
+  switch (dtype) {
+    case 0: return (void*)combinatoric_kernel<RealF>;
+    case 1: return (void*)combinatoric_kernel<CplxF>;
+    case 2: return (void*)combinatoric_kernel<IntF<unsigned char>>;
+    case 3: return (void*)combinatoric_kernel<IntF<long long>>;
+    default: return nullptr;
+  }
+}
+
+size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : 16; }
+
+}  // namespace
+
+int combinatoric_blocks_per_sm(int m, int n, int dtype, int block) {
+  void* k = pick(dtype);
+  if (!k) return 0;
+  size_t smem = (size_t)m * n * elem_bytes(dtype);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64_t prefixes, const LaunchCfg& c) {
+  void* k = pick(dtype);
+  if (!k) return cudaErrorInvalidValue;
+  size_t smem = (size_t)a.m * a.n * elem_bytes(dtype);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  SweepArgs args = a;
+  int d = depth;
+  uint64_t p = prefixes;
+  void* params[] = {&args, &d, &p};
+  return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
+}
+
+}  // namespace perm

@@ -35,6 +35,19 @@ constexpr int kIntRecord = 2;
 cudaError_t launch_glynn_f64(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
 int glynn_f64_blocks_per_sm(int n, int block, bool want_abs);
 
+// --- Glynn, real input on the integer pipes (glynn_fx.cu)
+// Quantised +-2q table (row i, column j at d[i * 64 + j]) and the exponents the
+// preparation kernel derives on the device.
+struct FxTable {
+  long long d[64 * 64];
+  int e_max;  // sum_j x_j with sum_i |a'_ij| < 2^x_j
+  int e_sum;  // sum_j e_j (column j scaled by 2^e_j)
+  int bad;    // a non-finite entry was seen
+  int pad;
+};
+cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
+int glynn_fx_blocks_per_sm(int n, int block, bool want_abs);
+
 // --- Glynn, complex FP64 (glynn_c128.cu); n <= glynn_c128_max_n()
 cudaError_t launch_glynn_c128(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
 int glynn_c128_blocks_per_sm(int n, int block, bool want_abs);
@@ -55,6 +68,45 @@ struct SizeWeights {
 cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, const LaunchCfg& c, bool want_abs);
 int ryser_f64_blocks_per_sm(int m, int n, int block, bool weighted, bool want_abs);
 
+// --- combinatoric algorithm (combinatoric.cu); dtype as perm_dtype
+cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64_t prefixes, const LaunchCfg& c);
+int combinatoric_blocks_per_sm(int m, int n, int dtype, int block);
+
+// --- batched Glynn (batched.cu)
+struct BatchItem {
+  int first;  // position in `order` of the (first) matrix
+  int count;  // lane items: number of matrices (<= 32); warp items: sub-range index
+  int parts;  // warp items: number of sub-ranges of the matrix (1 = whole)
+  int pad;
+};
+struct ClassWork {
+  const BatchItem* items;  // this class's items, longest first
+  int nitems;
+  int* counter;            // next item (zeroed before the launch)
+};
+struct BatchArgs {
+  const double* packed;     // elements of all matrices (complex: (re, im) pairs)
+  const int64_t* offsets;   // element offset of matrix b
+  const int32_t* M;         // rows of matrix b (row-major, leading dimension N[b])
+  const int32_t* N;         // columns of matrix b
+  const int32_t* order;     // matrices in item order
+  const int32_t* part_base; // first partial slot of matrix b (split matrices)
+  double* partials;         // 4 doubles per slot
+  int* done;                // sub-ranges finished per matrix (zeroed before the launch)
+  double* out;              // results (complex: (re, im) pairs)
+  int chunk_log2;
+};
+cudaError_t launch_batched_class(const BatchArgs& a, const ClassWork& c, int dtype, int npad, bool lane,
+                                 const LaunchCfg& lc);
+int batched_blocks_per_sm(int dtype, int npad, bool lane, int block);
+}  // namespace perm
+struct perm_handle_s;
+namespace perm {
+// host orchestration of perm_batched (batched_host.cu)
+int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);
+void batched_release(perm_handle_s* h);
+
 // --- final reductions (reduce.cu)
 // Sum `nrec` real records in a fixed order, scale by 2^-pow2 / fact (fact = (n-m)!,
 // given as the integer whose factorial divides), write result (and error bound).
@@ -66,6 +118,9 @@ cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_o
                                double* err, bool raw, cudaStream_t s);
 cudaError_t launch_finish_int(const unsigned long long* rec, int nrec, int pow2, int fact_of, unsigned long long* out,
                               bool raw, cudaStream_t s);
+
+// Write one double (e.g. -1 for "no error bound") to device memory.
+cudaError_t launch_write_double(double v, double* p, cudaStream_t s);
 
 // Write a constant result (used for m == 0, per = 1) for a dtype code.
 cudaError_t launch_write_one(int dtype, void* out, cudaStream_t s);

@@ -92,6 +92,8 @@ __global__ void finish_int_kernel(const unsigned long long* rec, int nrec, int p
   out[1] = (unsigned long long)(total >> 64);
 }
 
+__global__ void write_double_kernel(double v, double* p) { p[0] = v; }
+
 __global__ void write_one_kernel(int dtype, void* out) {
   if (dtype == 0) {
     static_cast<double*>(out)[0] = 1.0;
@@ -121,6 +123,11 @@ cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_o
 cudaError_t launch_finish_int(const unsigned long long* rec, int nrec, int pow2, int fact_of, unsigned long long* out,
                               bool raw, cudaStream_t s) {
   finish_int_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, out, raw ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_double(double v, double* p, cudaStream_t s) {
+  write_double_kernel<<<1, 1, 0, s>>>(v, p);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,111 @@
+"""Parity of perm_batched (persistent size-class kernels in one CUDA graph) with the
+CPU oracle and with the single-matrix path."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import close, device
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+def pack(mats, dtype):
+    offsets = np.zeros(len(mats), dtype=np.int64)
+    M = np.array([a.shape[0] for a in mats], dtype=np.int32)
+    N = np.array([a.shape[1] for a in mats], dtype=np.int32)
+    sizes = np.array([a.size for a in mats], dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes)[:-1]
+    packed = np.concatenate([np.ascontiguousarray(a, dtype=dtype).reshape(-1) for a in mats] + [np.zeros(1, dtype)])
+    return packed, offsets, M, N
+
+
+def to_torch(dev, *arrs):
+    import torch
+    return [torch.from_numpy(a).to(dev) for a in arrs]
+
+
+def results(capi, out, code, count):
+    return [capi.value(out, code, i) for i in range(count)]
+
+
+def mixed_batch(kind, seed, count=160):
+    g = inputs.rng(seed)
+    mats = []
+    for k in range(count):
+        m, n = int(g.integers(0, 13)), int(g.integers(1, 13))
+        if kind == "real":
+            mats.append(g.uniform(-1, 1, (m, n)))
+        else:
+            mats.append((g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))) / np.sqrt(2 * max(n, 1)))
+    return mats
+
+
+@pytest.mark.parametrize("kind", ["real", "complex"])
+def test_mixed_shapes_vs_oracle(capi, dev, kind):
+    import torch
+    mats = mixed_batch(kind, 9500 if kind == "real" else 9501)
+    dt = np.float64 if kind == "real" else np.complex128
+    packed, offsets, M, N = pack(mats, dt)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN)
+    torch.cuda.synchronize(dev)
+    code = capi.PERM_F64 if kind == "real" else capi.PERM_C128
+    got = results(capi, out, code, len(mats))
+    for A, x in zip(mats, got):
+        close(x, oracle.glynn(A), A)
+
+
+def test_haar_blocks_split_items_and_host_buffers(capi, dev):
+    import torch
+    sizes, packed, offsets = inputs.batched_haar(96, 4, 20, 9601)
+    M = sizes.astype(np.int32)
+    N = sizes.astype(np.int32)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN, opts=dict(chunk_log2=10))
+    torch.cuda.synchronize(dev)
+    got = results(capi, out, capi.PERM_C128, len(sizes))
+    for b, n in enumerate(sizes):
+        A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
+        single = capi.value(capi.perm_glynn(torch.from_numpy(A).to(dev)), capi.PERM_C128)
+        close(got[b], single, A)
+        if n <= 13:
+            close(got[b], oracle.glynn(A), A)
+    host_out = capi.perm_batched(packed, offsets, M, N)  # numpy in, numpy out
+    for b in range(len(sizes)):
+        close(capi.value(host_out, capi.PERM_C128, b), got[b], packed[offsets[b]: offsets[b] + sizes[b] ** 2])
+
+
+def test_graph_replay_sees_new_data(capi, dev):
+    import torch
+    mats = [inputs.uniform_real(n, n, 9700 + n) for n in (3, 7, 11, 15, 18)]
+    packed, offsets, M, N = pack(mats, np.float64)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = torch.empty(len(mats), dtype=torch.float64, device=dev)
+    capi.perm_batched(tp, to, tM, tN, out=out)
+    first = out.cpu().numpy().copy()
+    capi.perm_batched(tp, to, tM, tN, out=out)  # replay of the cached graph
+    assert np.array_equal(first, out.cpu().numpy())
+    tp.mul_(0.5)  # per(c A) = c^n per(A)
+    capi.perm_batched(tp, to, tM, tN, out=out)
+    torch.cuda.synchronize(dev)
+    for k, A in enumerate(mats):
+        close(float(out[k].item()), first[k] * 0.5 ** A.shape[0], A)
+
+
+def test_limits(capi, dev):
+    packed, offsets, M, N = pack([np.ones((33, 33))], np.float64)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_batched(packed, offsets, M, N)
+    assert e.value.status == capi.PERM_ETOOBIG

@@ -1,0 +1,70 @@
+"""Parity of the combinatoric algorithm (perm_combinatoric) with the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import close, device, run
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 6), (2, 2), (3, 3), (4, 6), (5, 5), (6, 9), (8, 8), (9, 9)])
+def test_dense_real_vs_definition(capi, dev, m, n):
+    A = inputs.uniform_real(m, n, 8000 + 31 * m + n)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A), A)
+
+
+def test_dense_real_12(capi, dev):
+    A = inputs.uniform_real(12, 12, 8101)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.glynn(A), A)
+
+
+@pytest.mark.parametrize("density", [0.15, 0.3])
+def test_sparse_real_16(capi, dev, density):
+    # the work cap counts dense leaves (16!); a sparse input is pruned, so raise it
+    A = inputs.sparse_real(16, 16, density, 8200 + int(100 * density))
+    close(run(capi, "perm_combinatoric", A, dev, dict(max_terms=1 << 62)), oracle.glynn(A), A)
+
+
+def test_transposed_and_complex(capi, dev):
+    A = inputs.uniform_real(7, 4, 8301)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A.T), A)
+    C = inputs.complex_gaussian(7, 7, 8302)
+    close(run(capi, "perm_combinatoric", C, dev), oracle.definition(C), C)
+
+
+@pytest.mark.parametrize("n", [3, 7, 10])
+def test_integers_exact(capi, dev, n):
+    B = inputs.bernoulli01(n, n, 8400 + n, 0.6)
+    assert run(capi, "perm_combinatoric", B, dev) == oracle.subset_dp(B.astype(np.int64))
+    Z = inputs.rng(8500 + n).integers(-20, 21, (n - 1, n)).astype(np.int64)
+    assert run(capi, "perm_combinatoric", Z, dev) == oracle.subset_dp(Z)
+
+
+def test_structure(capi, dev):
+    assert run(capi, "perm_combinatoric", np.eye(14), dev) == 1.0
+    A = inputs.uniform_real(9, 9, 8601)
+    A[4] = 0.0
+    assert run(capi, "perm_combinatoric", A, dev) == 0.0
+    assert run(capi, "perm_combinatoric", np.ones((6, 10), dtype=np.uint8), dev) == math.factorial(10) // math.factorial(4)
+
+
+def test_work_cap(capi, dev):
+    A = inputs.uniform_real(20, 20, 8701)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_combinatoric(A)
+    assert e.value.status == capi.PERM_ETOOBIG
