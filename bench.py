@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--n", type=int, default=36, help="matrix order (36 is the benchmark workload)")
     ap.add_argument("--arith", default="auto", choices=["auto", "fp64", "fixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched 100,000-matrix leg")
+    ap.add_argument("--batch-count", type=int, default=100000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -165,6 +167,57 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched leg
+def run_batched(args, dev, stream):
+    """100,000 complex128 n x n blocks of Haar unitaries (n uniform in 4..20): one
+    perm_batched graph launch per step, against one perm_glynn call per matrix."""
+    import numpy as np
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    count = args.batch_count
+    sizes, packed, offsets = inputs.batched_haar(count, 4, 20, inputs.SEED_BASE + 4)
+    M = sizes.astype(np.int32)
+    tp = torch.from_numpy(packed).to(dev)
+    to = torch.from_numpy(offsets).to(dev)
+    tM = torch.from_numpy(M).to(dev)
+    out = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            capi.perm_batched(tp, to, tM, tM, out=out, stream=stream)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            capi.perm_batched(tp, to, tM, tM, out=out, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+    batched_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # plain: one perm_glynn launch per matrix on the same stream
+    views = [tp[int(offsets[b]): int(offsets[b]) + int(sizes[b]) ** 2].view(int(sizes[b]), int(sizes[b]))
+             for b in range(count)]
+    plain = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    outs = [plain[b] for b in range(count)]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for b in range(count):
+        capi.perm_glynn(views[b], out=outs[b], stream=stream)
+    stream.synchronize()
+    plain_s = time.perf_counter() - t0
+    a = out.cpu().numpy()
+    p = plain.cpu().numpy()
+    za, zp = a[:, 0] + 1j * a[:, 1], p[:, 0] + 1j * p[:, 1]
+    rel = float(np.max(np.abs(za - zp) / np.maximum(np.abs(zp), 1e-300)))
+    terms = float(np.sum(2.0 ** (sizes.astype(np.float64) - 1)))
+    return {"workload": "%d complex128 n x n leading blocks of Haar unitaries (order 64), n uniform in 4..20" % count,
+            "perms_per_s": count / (batched_ms * 1e-3), "ms_per_batch": batched_ms,
+            "terms_per_s": terms / (batched_ms * 1e-3),
+            "plain_perms_per_s": count / plain_s, "plain_s": plain_s,
+            "speedup_vs_plain": plain_s / (batched_ms * 1e-3),
+            "max_rel_diff_vs_plain": rel, "arith": "fp64 (complex), Kahan-compensated",
+            "launch": "one CUDA graph (size-class kernels on parallel branches)"}
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -250,6 +303,9 @@ def run_ours(args):
         "gpu_launches": 2 * args.steps,
         "clocks": clocks.summary(),
     }
+    if not args.no_batched:
+        side = torch.cuda.Stream(dev)
+        line["batched"] = run_batched(args, dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         rate, tt, wall = cpu_oracle_rate(A, args.cpu_seconds, cores)

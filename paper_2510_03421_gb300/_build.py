@@ -69,6 +69,9 @@ def build(verbose: bool = False, extra_flags=(), jobs: int | None = None) -> str
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
+    for old in glob.glob(os.path.join(BUILD, "*.o")):  # objects of earlier source versions
+        if old not in objs:
+            os.remove(old)
     stamp = hashlib.sha1("".join(objs).encode()).hexdigest()[:16]
     stamp_file = os.path.join(BUILD, "libperm.stamp")
     if os.path.exists(LIB) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:

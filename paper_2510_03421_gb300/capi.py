@@ -24,7 +24,12 @@ PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED = 0, 1, 2
 PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
-           "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status")
+           "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status",
+           "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
+           "perm_set_cost_model", "perm_auto_choice")
+PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
+PERM_NCAND = 4
+PERM_NFEATURES = 12
 PROBE_DFMA, PROBE_DMMA, PROBE_IMAD, PROBE_IADD, PROBE_FFMA = range(5)
 
 
@@ -62,6 +67,15 @@ def lib():
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
             L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+            fp = ctypes.c_void_p
+            L.perm_auto_features.argtypes = [i64, i64, ctypes.c_double, i32, fp]
+            L.perm_mlp_size.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_int64)]
+            L.perm_mlp_forward.argtypes = [fp, i32, i32, i32, fp, i64, fp, vp]
+            L.perm_mlp_grad.argtypes = [fp, i32, i32, i32, fp, fp, fp, i64, fp, fp, vp]
+            L.perm_mlp_train.argtypes = [fp, fp, fp, i64, i32, i32, i32, i32, i32, ctypes.c_float, u64, fp, fp, vp]
+            L.perm_set_cost_model.argtypes = [vp, fp, i32, i32, i32]
+            L.perm_auto_choice.argtypes = [vp, vp, i64, i64, i64, i32, ctypes.POINTER(perm_opts),
+                                           ctypes.POINTER(ctypes.c_int), fp]
             L.perm_probe_rate.argtypes = [i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
             L.perm_status_string.argtypes = [i32]
             L.perm_status_string.restype = ctypes.c_char_p
@@ -248,6 +262,77 @@ def perm_glynn_noalloc(A, out=None, stream=None, grid: int = 0):
     if rc:
         raise PermError(rc, "perm_glynn_noalloc")
     return out
+
+
+def _check(rc, name):
+    if rc:
+        raise PermError(rc, name)
+
+
+def perm_auto_features(m: int, n: int, density: float, code: int):
+    out = np.zeros(PERM_NFEATURES, dtype=np.float32)
+    _check(lib().perm_auto_features(m, n, density, code, out.ctypes.data), "perm_auto_features")
+    return out
+
+
+def perm_mlp_size(in_dim: int, hidden: int, out_dim: int) -> int:
+    c = ctypes.c_int64()
+    _check(lib().perm_mlp_size(in_dim, hidden, out_dim, ctypes.byref(c)), "perm_mlp_size")
+    return c.value
+
+
+def perm_mlp_forward(weights, dims, X, Y=None, stream=None):
+    """Y = MLP(X) on the GPU; weights, X, Y are float32 CUDA tensors."""
+    import torch
+    in_dim, hid, out_dim = dims
+    if Y is None:
+        Y = torch.empty((X.shape[0], out_dim), dtype=torch.float32, device=X.device)
+    _check(lib().perm_mlp_forward(weights.data_ptr(), in_dim, hid, out_dim, X.data_ptr(), X.shape[0], Y.data_ptr(),
+                                  _stream(X.device, stream)), "perm_mlp_forward")
+    return Y
+
+
+def perm_mlp_grad(weights, dims, X, T, mask, stream=None):
+    """(gradient, loss) of the masked MSE with respect to the flat weights (CUDA tensors)."""
+    import torch
+    in_dim, hid, out_dim = dims
+    grad = torch.empty_like(weights)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(lib().perm_mlp_grad(weights.data_ptr(), in_dim, hid, out_dim, X.data_ptr(), T.data_ptr(), mask.data_ptr(),
+                               X.shape[0], grad.data_ptr(), loss.data_ptr(), _stream(X.device, stream)),
+           "perm_mlp_grad")
+    return grad, loss
+
+
+def perm_mlp_train(X, T, mask, dims, epochs: int, batch: int, lr: float, seed: int, stream=None):
+    """Train on the GPU; returns (weights, per-epoch loss) as CUDA tensors."""
+    import torch
+    in_dim, hid, out_dim = dims
+    weights = torch.empty(perm_mlp_size(in_dim, hid, out_dim), dtype=torch.float32, device=X.device)
+    hist = torch.zeros(max(epochs, 1), dtype=torch.float32, device=X.device)
+    _check(lib().perm_mlp_train(X.data_ptr(), T.data_ptr(), mask.data_ptr(), X.shape[0], in_dim, hid, out_dim, epochs,
+                                batch, lr, seed, weights.data_ptr(), hist.data_ptr(), _stream(X.device, stream)),
+           "perm_mlp_train")
+    return weights, hist
+
+
+def perm_set_cost_model(weights, dims, device: int = 0):
+    """Install host float32 weights (numpy) as perm_auto's cost model; None removes it."""
+    if weights is None:
+        _check(lib().perm_set_cost_model(handle(device), None, 0, 0, 0), "perm_set_cost_model")
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(lib().perm_set_cost_model(handle(device), w.ctypes.data, *dims), "perm_set_cost_model")
+
+
+def perm_auto_choice(A, opts=None):
+    """(candidate, predicted log2 seconds per candidate) that perm_auto would use."""
+    keep, p, m, n, ld, code, dev = _matrix(A)
+    cand = ctypes.c_int(-1)
+    pred = np.zeros(PERM_NCAND, dtype=np.float32)
+    _check(lib().perm_auto_choice(handle(_device_index(dev)), p, m, n, ld, code, _opts(opts), ctypes.byref(cand),
+                                  pred.ctypes.data), "perm_auto_choice")
+    return cand.value, pred
 
 
 def perm_probe_rate(kind: int, device: int = 0, stream=None) -> float:

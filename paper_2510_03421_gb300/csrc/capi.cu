@@ -3,10 +3,13 @@
 #include <cstdint>
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 #include <new>
 
 #include "../../include/perm.h"
+#include "../../include/perm_mlp.h"
 #include "internal.h"
 
 #include "handle.h"
@@ -374,6 +377,152 @@ int combinatoric_run(Call& c) {
   return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
+// ---------------------------------------------------------------- learned dispatch
+double log2_perm_nodes(int m, int n, double density) {
+  // log2 of sum_{k=1..m} n!/(n-k)! density^k: nodes of the pruned search tree
+  double total = 0.0, term = 1.0;
+  for (int k = 1; k <= m; ++k) {
+    term *= (double)(n - k + 1) * density;
+    total += term;
+  }
+  return total > 1.0 ? std::log2(total) : 0.0;
+}
+
+void features(int m, int n, double density, int dtype, float* f) {
+  const double mm = m, nn = n > 0 ? n : 1;
+  f[0] = (float)(mm / 64.0);
+  f[1] = (float)(nn / 64.0);
+  f[2] = (float)(mm / nn);
+  f[3] = (float)density;
+  f[4] = (float)(((double)(n - 1) + std::log2(nn)) / 64.0);             // Glynn: 2^(n-1) terms of n columns
+  f[5] = (float)(((double)n + std::log2(mm > 0 ? mm : 1.0)) / 64.0);    // Ryser: 2^n subsets of m rows
+  f[6] = (float)(log2_perm_nodes(m, n, 1.0) / 64.0);                   // combinatoric, dense
+  f[7] = (float)(log2_perm_nodes(m, n, density) / 64.0);               // combinatoric, pruned
+  f[8] = dtype == PERM_F64 ? 1.f : 0.f;
+  f[9] = dtype == PERM_C128 ? 1.f : 0.f;
+  f[10] = (dtype == PERM_U8 || dtype == PERM_I64) ? 1.f : 0.f;
+  f[11] = (float)((nn - mm) / 64.0);
+}
+
+// Which candidates exist for the dtype and stay under the work cap.
+void feasible(int m, int n, double density, int dtype, uint64_t cap, bool* ok) {
+  const double lcap = std::log2((double)cap);
+  ok[PERM_CAND_COMBINATORIC] = log2_perm_nodes(m, n, density) <= lcap;
+  ok[PERM_CAND_RYSER] = dtype == PERM_F64 && n <= 62 && (double)n <= lcap;
+  ok[PERM_CAND_GLYNN] = (double)(n - 1) <= lcap && (dtype != PERM_C128 || n <= glynn_c128_max_n());
+  ok[PERM_CAND_GLYNN_FIXED] = dtype == PERM_F64 && (double)(n - 1) <= lcap;
+}
+
+// Host-side inference of the installed model.
+void model_predict(const perm_handle h, const float* x, float* y) {
+  const int in = h->model_in, hid = h->model_hid, out = h->model_out;
+  const float* W1 = h->model.data();
+  const float* b1 = W1 + (size_t)in * hid;
+  const float* W2 = b1 + hid;
+  const float* b2 = W2 + (size_t)hid * hid;
+  const float* W3 = b2 + hid;
+  const float* b3 = W3 + (size_t)hid * out;
+  std::vector<float> a1(hid), a2(hid);
+  for (int o = 0; o < hid; ++o) {
+    float z = b1[o];
+    for (int i = 0; i < in; ++i) z = std::fma(x[i], W1[(size_t)i * hid + o], z);
+    a1[o] = z > 0.f ? z : 0.f;
+  }
+  for (int o = 0; o < hid; ++o) {
+    float z = b2[o];
+    for (int i = 0; i < hid; ++i) z = std::fma(a1[i], W2[(size_t)i * hid + o], z);
+    a2[o] = z > 0.f ? z : 0.f;
+  }
+  for (int o = 0; o < out; ++o) {
+    float z = b3[o];
+    for (int i = 0; i < hid; ++i) z = std::fma(a2[i], W3[(size_t)i * out + o], z);
+    y[o] = z;
+  }
+}
+
+// Fraction of nonzero entries of the operand (reads a host copy).
+int density_of(const Call& c, double* d) {
+  const size_t es = elem_size(c.dtype);
+  const size_t count = (size_t)c.m * c.n;
+  if (count == 0) {
+    *d = 1.0;
+    return PERM_OK;
+  }
+  std::vector<unsigned char> host(count * es);
+  // the operand is m x n with strides (rs, cs); copy element by element rows of the
+  // underlying buffer: the m x n block spans at most (m-1) rs + (n-1) cs + 1 elements
+  const int64_t span = (int64_t)(c.m - 1) * c.rs + (int64_t)(c.n - 1) * c.cs + 1;
+  std::vector<unsigned char> raw((size_t)span * es);
+  if (cudaMemcpyAsync(raw.data(), c.dA, raw.size(), cudaMemcpyDefault, c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  size_t nnz = 0;
+  for (int i = 0; i < c.m; ++i)
+    for (int j = 0; j < c.n; ++j) {
+      const unsigned char* e = raw.data() + (size_t)(i * c.rs + j * c.cs) * es;
+      bool nz = false;
+      for (size_t b = 0; b < es; ++b) nz |= (e[b] != 0);
+      if (c.dtype == PERM_F64 || c.dtype == PERM_C128) {  // -0.0 is zero
+        double v[2] = {0.0, 0.0};
+        std::memcpy(v, e, es);
+        nz = (v[0] != 0.0) || (v[1] != 0.0);
+      }
+      nnz += nz ? 1 : 0;
+    }
+  *d = (double)nnz / (double)count;
+  return PERM_OK;
+}
+
+// Candidate choice: the model's argmin over feasible candidates, or the built-in rule.
+int choose(perm_handle h, int m, int n, double density, int dtype, uint64_t cap, int* cand, float* pred) {
+  bool ok[PERM_NCAND];
+  feasible(m, n, density, dtype, cap, ok);
+  float y[PERM_NCAND];
+  const bool have_model = !h->model.empty() && h->model_in == PERM_NFEATURES && h->model_out == PERM_NCAND;
+  if (have_model) {
+    float x[PERM_NFEATURES];
+    features(m, n, density, dtype, x);
+    model_predict(h, x, y);
+  } else {
+    // built-in rule without the model: the combinatoric algorithm for very small
+    // matrices, Glynn (integer pipes for real input) otherwise
+    for (int k = 0; k < PERM_NCAND; ++k) y[k] = 0.f;
+    y[PERM_CAND_COMBINATORIC] = (n <= 6) ? -2.f : 2.f;
+    y[PERM_CAND_RYSER] = 3.f;
+    y[PERM_CAND_GLYNN] = dtype == PERM_F64 ? 1.f : 0.f;
+    y[PERM_CAND_GLYNN_FIXED] = 0.f;
+  }
+  int best = -1;
+  for (int k = 0; k < PERM_NCAND; ++k) {
+    if (!ok[k]) y[k] = INFINITY;
+    if (ok[k] && (best < 0 || y[k] < y[best])) best = k;
+  }
+  if (pred)
+    for (int k = 0; k < PERM_NCAND; ++k) pred[k] = y[k];
+  if (best < 0) return PERM_ETOOBIG;
+  *cand = best;
+  return PERM_OK;
+}
+
+int run_candidate(Call& c, int cand) {
+  switch (cand) {
+    case PERM_CAND_COMBINATORIC: {
+      Call cc = c;
+      cc.o.max_terms = ~0ull >> 2;  // feasibility was judged on the pruned tree
+      return combinatoric_run(cc);
+    }
+    case PERM_CAND_RYSER: return ryser_real(c);
+    case PERM_CAND_GLYNN: {
+      const uint64_t terms = 1ull << (c.n - 1);
+      if (c.dtype == PERM_F64) return glynn_fp64(c, false, 0, terms);
+      if (c.dtype == PERM_C128) return glynn_cplx(c, false, 0, terms);
+      return glynn_integer(c, false, 0, terms);
+    }
+    case PERM_CAND_GLYNN_FIXED: return glynn_fixed(c, false, 0, 1ull << (c.n - 1));
+    default: return PERM_EINVAL;
+  }
+}
+
 uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDefaultMaxTerms; }
 
 }  // namespace
@@ -530,7 +679,91 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
 
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
               const perm_opts* opts) {
-  return perm_glynn(h, A, m, n, ld, dtype, out, stream, opts);
+  Call c;
+  int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
+  if (rc) return rc;
+  if (c.m == 0) {
+    if (launch_write_one(dtype, c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+    return finish(c, out_size(dtype));
+  }
+  double density = 1.0;
+  rc = density_of(c, &density);
+  if (rc) return rc;
+  const uint64_t cap = max_terms(c.o);
+  int cand = 0;
+  if (c.o.exhaustive) {
+    // time every feasible candidate, then run the fastest last so `out` holds its result
+    bool ok[PERM_NCAND];
+    feasible(c.m, c.n, density, dtype, cap, ok);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PERM_ECUDA;
+    float best_ms = INFINITY;
+    int best = -1;
+    for (int k = 0; k < PERM_NCAND; ++k) {
+      if (!ok[k]) continue;
+      cudaEventRecord(e0, c.stream);
+      if (run_candidate(c, k) != PERM_OK) continue;
+      cudaEventRecord(e1, c.stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return PERM_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = k;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return PERM_ETOOBIG;
+    cand = best;
+  } else {
+    rc = choose(h, c.m, c.n, density, dtype, cap, &cand, nullptr);
+    if (rc) return rc;
+  }
+  rc = run_candidate(c, cand);
+  if (rc) return rc;
+  return finish(c, out_size(dtype));
+}
+
+int perm_auto_features(int64_t m, int64_t n, double density, int dtype, float* out) {
+  if (!out || m < 0 || n < 0 || m > 64 || n > 64 || !(density >= 0.0 && density <= 1.0)) return PERM_EINVAL;
+  if (m > n) std::swap(m, n);
+  features((int)m, (int)n, density, dtype, out);
+  return PERM_OK;
+}
+
+int perm_set_cost_model(perm_handle h, const float* weights, int32_t in_dim, int32_t hidden, int32_t out_dim) {
+  if (!h) return PERM_EINVAL;
+  if (!weights) {
+    h->model.clear();
+    return PERM_OK;
+  }
+  int64_t count = 0;
+  if (perm_mlp_size(in_dim, hidden, out_dim, &count) != PERM_OK) return PERM_EINVAL;
+  if (in_dim != PERM_NFEATURES || out_dim != PERM_NCAND) return PERM_EINVAL;
+  h->model.assign(weights, weights + count);
+  h->model_in = in_dim;
+  h->model_hid = hidden;
+  h->model_out = out_dim;
+  return PERM_OK;
+}
+
+int perm_auto_choice(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, const perm_opts* opts,
+                     int* candidate, float* predicted) {
+  if (!candidate) return PERM_EINVAL;
+  Call c;
+  double dummy_out[2];
+  int rc = prepare(c, h, A, m, n, ld, dtype, dummy_out, nullptr, opts, true);
+  if (rc) return rc;
+  if (c.m == 0) {
+    *candidate = PERM_CAND_GLYNN;
+    return PERM_OK;
+  }
+  double density = 1.0;
+  rc = density_of(c, &density);
+  if (rc) return rc;
+  return choose(h, c.m, c.n, density, dtype, max_terms(c.o), candidate, predicted);
 }
 
 int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,

@@ -39,4 +39,7 @@ struct perm_handle_s {
   perm::BatchTune tune;
   bool tuned = false;
   uint64_t tuned_hist = 0;      // size histogram the tune was chosen for
+  // cost model of perm_auto (host copy of the weights)
+  std::vector<float> model;
+  int model_in = 0, model_hid = 0, model_out = 0;
 };

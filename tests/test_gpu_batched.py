@@ -84,7 +84,8 @@ def test_haar_blocks_split_items_and_host_buffers(capi, dev):
             close(got[b], oracle.glynn(A), A)
     host_out = capi.perm_batched(packed, offsets, M, N)  # numpy in, numpy out
     for b in range(len(sizes)):
-        close(capi.value(host_out, capi.PERM_C128, b), got[b], packed[offsets[b]: offsets[b] + sizes[b] ** 2])
+        n = int(sizes[b])
+        close(capi.value(host_out, capi.PERM_C128, b), got[b], packed[offsets[b]: offsets[b] + n * n].reshape(n, n))
 
 
 def test_graph_replay_sees_new_data(capi, dev):
