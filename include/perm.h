@@ -137,6 +137,15 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
 int perm_glynn_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype,
                        uint64_t g_begin, uint64_t g_end, void* partial, void* stream, const perm_opts* opts);
 
+/* Partial Ryser sum over the column subsets g_begin <= g < g_end in reflected Gray-code
+ * order (subset(g) = set bits of gray(g) = g ^ (g >> 1), bit c <-> column c), each
+ * weighted as in the sum that perm_ryser evaluates: (-1)^(m-|S|) C(n-|S|, m-|S|)
+ * prod_i sum_{j in S} a_ij (Eq. ryser_rectangle; for m = n, Eq. ryser_square).  The
+ * sum over [0, 2^n) is per(A).  PERM_F64 only; m <= n required (no transpose);
+ * `partial` receives a double-double (hi, lo). */
+int perm_ryser_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype,
+                       uint64_t g_begin, uint64_t g_end, void* partial, void* stream, const perm_opts* opts);
+
 /* Real (PERM_F64) Glynn sweep for callers that cannot allocate device memory, such
  * as runtimes that hand out every buffer from a pool reserved up front or plugin
  * hosts that forbid cudaMalloc.  The paper has no counterpart; this is a deployment

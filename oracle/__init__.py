@@ -62,6 +62,7 @@ def _load():
                     getattr(lib, "oracle_ryser_square%s_%s" % (c, prec)).argtypes = [i, p, i64, p]
                     getattr(lib, "oracle_glynn_partial%s_%s" % (c, prec)).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_glynn_partial_abs_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_ryser_partial_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
             for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
             lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
@@ -183,6 +184,19 @@ def glynn_partial_abs(A, g0: int, g1: int, prec: str = "ld") -> float:
         raise ValueError("term range outside [0, 2^(n-1)]")
     out = (ctypes.c_double * 2)()
     getattr(lib, "oracle_glynn_partial_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
+    return float(out[0]) + float(out[1])
+
+
+def ryser_partial(A, g0: int, g1: int, prec: str = "ld") -> float:
+    """Weighted Ryser sum over the Gray-ordered column subsets g0 <= g < g1 (real input)."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind != "real":
+        raise TypeError("ryser_partial takes a real matrix")
+    if not (0 <= g0 <= g1 <= (1 << n)):
+        raise ValueError("subset range outside [0, 2^n]")
+    out = (ctypes.c_double * 2)()
+    getattr(lib, "oracle_ryser_partial_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
     return float(out[0]) + float(out[1])
 
 

@@ -26,7 +26,7 @@ PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
            "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status",
            "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
-           "perm_set_cost_model", "perm_auto_choice")
+           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial")
 PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
 PERM_NCAND = 4
 PERM_NFEATURES = 12
@@ -64,6 +64,7 @@ def lib():
             for name in ("perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto"):
                 getattr(L, name).argtypes = [vp, vp, i64, i64, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_ryser_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
             L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
@@ -233,6 +234,22 @@ def perm_glynn_partial(A, g_begin: int, g_end: int, out=None, stream=None, opts=
                                   _stream(dev, stream), _opts(opts))
     if rc:
         raise PermError(rc, "perm_glynn_partial")
+    return out
+
+
+def perm_ryser_partial(A, g_begin: int, g_end: int, out=None, stream=None, opts=None):
+    """Weighted Ryser sum over the Gray-ordered subsets [g_begin, g_end) (double-double)."""
+    keep, p, m, n, ld, code, dev = _matrix(A)
+    if out is None:
+        if dev is not None:
+            import torch
+            out = torch.empty(2, dtype=torch.float64, device=dev)
+        else:
+            out = np.empty(2, dtype=np.float64)
+    rc = lib().perm_ryser_partial(handle(_device_index(dev)), p, m, n, ld, code, g_begin, g_end, _ptr(out),
+                                  _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_ryser_partial")
     return out
 
 

@@ -195,7 +195,37 @@ LaunchCfg plan_grid(perm_handle h, const perm_opts& o, int block, int bps, uint6
   return lc;
 }
 
+SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk);
+
+// Real Glynn with the chunk-start column sums formed by a +-1 x A' contraction on the
+// FP64 tensor cores (glynn_dmma.cu).
+int glynn_dmma(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.n > glynn_dmma_max_n()) return PERM_EUNSUPPORTED;
+  const bool want_abs = c.dErr != nullptr;
+  const int block = c.o.block ? c.o.block : 256;
+  int bps = glynn_dmma_blocks_per_sm(c.n, block, want_abs);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 32, kRealRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, g0, g1, 14);
+  if (!c.o.chunk_log2) {
+    // chunks of 2^k terms, at least four rounds of 32 chunks per resident warp
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 16;
+    while (k > 2 && ((g1 - g0) >> k) < 128 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  if (launch_glynn_dmma(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  const double u = 1.1102230246251565e-16;
+  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
+  const double coef = u * ((double)c.n + 4.0 + 2.0 * (double)c.n * L);
+  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
 int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.o.start == PERM_START_DMMA) return glynn_dmma(c, raw, g0, g1);
   const bool want_abs = c.dErr != nullptr;
   const int block = 256;
   int bps = glynn_f64_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
@@ -224,7 +254,6 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   return PERM_OK;
 }
 
-SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk);
 
 // Real Glynn on the integer pipes: exact fixed-point column sums, 64-bit-mantissa
 // products, 192-bit accumulation (glynn_fx.cu).
@@ -313,9 +342,10 @@ double binomial_d(int a, int b) {
 
 // Ryser over the 2^n column subsets (square: Eq. ryser_square; m < n: the subset-size
 // weights of Eq. ryser_rectangle).
-int ryser_real(Call& c) {
+int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
   if (c.n > 62) return PERM_ETOOBIG;
-  const uint64_t terms = 1ull << c.n;
+  const uint64_t terms = raw ? g1 - g0 : (1ull << c.n);
+  if (!raw) g1 = terms;
   if (terms > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
   const bool want_abs = c.dErr != nullptr;
   const bool weighted = c.m < c.n;
@@ -323,7 +353,7 @@ int ryser_real(Call& c) {
   int bps = ryser_f64_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, weighted, want_abs);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, kRealRecord * sizeof(double));
   lc.stream = c.stream;
-  SweepArgs a = sweep_args(c, 0, terms, 14);
+  SweepArgs a = sweep_args(c, g0, g1, 14);
   SizeWeights w;
   for (int s = 0; s <= 64; ++s) {
     w.w[s] = 0.0;
@@ -335,9 +365,57 @@ int ryser_real(Call& c) {
   const double coef = u * ((double)c.m + 5.0 + 2.0 * (double)c.m * L);
   const double sign = (!weighted && (c.n & 1)) ? -1.0 : 1.0;
   if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef, static_cast<double*>(c.dOut),
-                         c.dErr, false, c.stream, sign) != cudaSuccess)
+                         c.dErr, raw, c.stream, sign) != cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
+}
+
+// Ryser for complex and integer input (ryser_ext.cu): all weights carry the sign.
+int ryser_other(Call& c) {
+  if (c.n > 62) return PERM_ETOOBIG;
+  const uint64_t terms = 1ull << c.n;
+  if (terms > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
+  if (c.dtype == PERM_C128 && c.m > 40) return PERM_EUNSUPPORTED;
+  const int block = c.dtype == PERM_C128 ? 128 : 256;
+  if (c.o.block > block) return PERM_EINVAL;
+  int bps = ryser_ext_blocks_per_sm(c.m, c.n, c.dtype, c.o.block ? c.o.block : block);
+  const size_t rec = c.dtype == PERM_C128 ? kCplxRecord * 8 : kIntRecord * 8;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, rec);
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, terms, 14);
+  SizeWeights fw;
+  IntWeights iw;
+  for (int s = 0; s <= 64; ++s) {
+    fw.w[s] = 0.0;
+    iw.lo[s] = iw.hi[s] = 0;
+    if (s <= c.m) {
+      unsigned __int128 b = 1;
+      for (int i = 1; i <= c.m - s; ++i) b = b * (unsigned __int128)(c.n - s - (c.m - s) + i) / (unsigned __int128)i;
+      const bool neg = ((c.m - s) & 1) != 0;
+      fw.w[s] = (neg ? -1.0 : 1.0) * (double)b;
+      const unsigned __int128 v = neg ? (unsigned __int128)0 - b : b;
+      iw.lo[s] = (unsigned long long)v;
+      iw.hi[s] = (unsigned long long)(v >> 64);
+    }
+  }
+  if (c.dtype != PERM_C128) {
+    int* st = c.hOut ? call_status_word(c.h) : status_word(c.h);
+    if (c.hOut && cudaMemsetAsync(st, 0, sizeof(int), c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, st, c.stream) != cudaSuccess) return PERM_ECUDA;
+  }
+  if (launch_ryser_ext(a, c.dtype, fw, iw, lc) != cudaSuccess) return PERM_ECUDA;
+  cudaError_t e;
+  if (c.dtype == PERM_C128) {
+    const double u = 1.1102230246251565e-16;
+    e = launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, 0, 0, u, static_cast<double*>(c.dOut),
+                           nullptr, false, c.stream);
+    if (e == cudaSuccess && c.dErr) e = launch_write_double(-1.0, c.dErr, c.stream);
+  } else {
+    e = launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, 0, 0,
+                          static_cast<unsigned long long*>(c.dOut), false, c.stream);
+    if (e == cudaSuccess && c.dErr) e = cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream);
+  }
+  return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
 // The combinatoric algorithm over all injective maps (combinatoric.cu).
@@ -644,6 +722,20 @@ int perm_glynn_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64
   return finish(c, bytes);
 }
 
+int perm_ryser_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, uint64_t g_begin,
+                       uint64_t g_end, void* partial, void* stream, const perm_opts* opts) {
+  Call c;
+  if (m > n || m < 1) return PERM_EINVAL;
+  if (dtype != PERM_F64) return PERM_EUNSUPPORTED;
+  int rc = prepare(c, h, A, m, n, ld, dtype, partial, stream, opts, false);
+  if (rc) return rc;
+  if (c.n > 62) return PERM_ETOOBIG;
+  if (g_begin > g_end || g_end > (1ull << c.n)) return PERM_EINVAL;
+  rc = ryser_real(c, true, g_begin, g_end);
+  if (rc) return rc;
+  return finish(c, 16);
+}
+
 int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
                const perm_opts* opts) {
   Call c;
@@ -656,7 +748,7 @@ int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
   }
   switch (dtype) {
     case PERM_F64: rc = ryser_real(c); break;
-    default: return PERM_EUNSUPPORTED;
+    default: rc = ryser_other(c); break;
   }
   if (rc) return rc;
   return finish(c, out_size(dtype));

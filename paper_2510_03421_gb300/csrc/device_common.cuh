@@ -77,6 +77,21 @@ __device__ __forceinline__ void block_sum_dd(dd (&v)[K], dd* scratch) {
   }
 }
 
+// ---------------------------------------------------------------- products
+// prod_j x_j as a balanced tree of FP64 multiplications (N - 1 of them).
+template <int N>
+__device__ __forceinline__ double product_tree(const double (&x)[N]) {
+  constexpr int H = (N + 1) / 2;
+  double p[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) p[j] = (2 * j + 1 < N) ? __dmul_rn(x[2 * j], x[2 * j + 1]) : x[2 * j];
+#pragma unroll
+  for (int w = 1; w < H; w *= 2)
+#pragma unroll
+    for (int j = 0; j + w < H; j += 2 * w) p[j] = __dmul_rn(p[j], p[j + w]);
+  return p[0];
+}
+
 // ---------------------------------------------------------------- work split
 // Split [g_begin, g_end) into `parts` nearly equal contiguous ranges; range `t`
 // is [*lo, *lo + *len).

@@ -23,18 +23,6 @@
 namespace perm {
 namespace {
 
-template <int N>
-__device__ __forceinline__ double product_tree(const double (&S)[N]) {
-  constexpr int H = (N + 1) / 2;
-  double p[H];
-#pragma unroll
-  for (int j = 0; j < H; ++j) p[j] = (2 * j + 1 < N) ? __dmul_rn(S[2 * j], S[2 * j + 1]) : S[2 * j];
-#pragma unroll
-  for (int w = 1; w < H; w *= 2)
-#pragma unroll
-    for (int j = 0; j + w < H; j += 2 * w) p[j] = __dmul_rn(p[j], p[j + w]);
-  return p[0];
-}
 
 template <int N, bool ABS>
 __global__ void __launch_bounds__(256) glynn_f64_kernel(SweepArgs a) {

@@ -35,6 +35,11 @@ constexpr int kIntRecord = 2;
 cudaError_t launch_glynn_f64(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
 int glynn_f64_blocks_per_sm(int n, int block, bool want_abs);
 
+// --- Glynn, real FP64 with chunk-start column sums on the FP64 tensor cores (glynn_dmma.cu)
+cudaError_t launch_glynn_dmma(const SweepArgs& a, const LaunchCfg& c, bool want_abs);
+int glynn_dmma_blocks_per_sm(int n, int block, bool want_abs);
+int glynn_dmma_max_n();
+
 // --- Glynn, real input on the integer pipes (glynn_fx.cu)
 // Quantised +-2q table (row i, column j at d[i * 64 + j]) and the exponents the
 // preparation kernel derives on the device.
@@ -66,6 +71,15 @@ struct SizeWeights {
   double w[65];
 };
 cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, const LaunchCfg& c, bool want_abs);
+// exact weights for the integer Ryser sweep, as two's-complement int128 halves
+struct IntWeights {
+  unsigned long long lo[65];
+  unsigned long long hi[65];
+};
+// complex (dtype 1, m <= 40) and integer (dtype 2 / 3) Ryser sweeps (ryser_ext.cu)
+cudaError_t launch_ryser_ext(const SweepArgs& a, int dtype, const SizeWeights& fw, const IntWeights& iw,
+                             const LaunchCfg& c);
+int ryser_ext_blocks_per_sm(int m, int n, int dtype, int block);
 int ryser_f64_blocks_per_sm(int m, int n, int block, bool weighted, bool want_abs);
 
 // --- combinatoric algorithm (combinatoric.cu); dtype as perm_dtype

@@ -16,18 +16,6 @@
 namespace perm {
 namespace {
 
-template <int M>
-__device__ __forceinline__ double product_tree(const double (&R)[M]) {
-  constexpr int H = (M + 1) / 2;
-  double p[H];
-#pragma unroll
-  for (int j = 0; j < H; ++j) p[j] = (2 * j + 1 < M) ? __dmul_rn(R[2 * j], R[2 * j + 1]) : R[2 * j];
-#pragma unroll
-  for (int w = 1; w < H; w *= 2)
-#pragma unroll
-    for (int j = 0; j + w < H; j += 2 * w) p[j] = __dmul_rn(p[j], p[j + w]);
-  return p[0];
-}
 
 template <int M, bool WEIGHTED, bool ABS>
 __global__ void __launch_bounds__(256) ryser_f64_kernel(SweepArgs a, SizeWeights weights) {

@@ -1,0 +1,142 @@
+"""The learned dispatcher: the GPU perceptron kernels against the float64 reference
+(oracle/mlp_ref.py), perm_auto's results against the CPU oracle, the Ryser partial
+sums, and what a model trained on this library's timings gains over dispatch
+without it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import close, device, run, to_dev
+from oracle import mlp_ref
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (12, 32, 4)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+def _data(seed, rows=300):
+    g = inputs.rng(seed)
+    n = 12 * 32 + 32 + 32 * 32 + 32 + 32 * 4 + 4
+    w = g.normal(0, 0.3, n).astype(np.float32)
+    X = g.normal(0, 1, (rows, 12)).astype(np.float32)
+    T = g.normal(0, 1, (rows, 4)).astype(np.float32)
+    M = (g.random((rows, 4)) < 0.8).astype(np.float32)
+    return w, X, T, M
+
+
+def test_forward_matches_reference(capi, dev):
+    import torch
+    w, X, T, M = _data(11)
+    y = capi.perm_mlp_forward(torch.from_numpy(w).to(dev), DIMS, torch.from_numpy(X).to(dev))
+    ref, _ = mlp_ref.forward(w.astype(np.float64), DIMS, X.astype(np.float64))
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+def test_gradient_matches_reference(capi, dev):
+    import torch
+    w, X, T, M = _data(12)
+    g, loss = capi.perm_mlp_grad(*[torch.from_numpy(a).to(dev) for a in (w,)], DIMS,
+                                 *[torch.from_numpy(a).to(dev) for a in (X, T, M)])
+    ref = mlp_ref.grad(w.astype(np.float64), DIMS, X.astype(np.float64), T.astype(np.float64), M.astype(np.float64))
+    got = g.cpu().numpy().astype(np.float64)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 2e-4 * scale
+    lref = mlp_ref.loss(w.astype(np.float64), DIMS, X.astype(np.float64), T.astype(np.float64), M.astype(np.float64))
+    assert abs(float(loss.item()) - lref) <= 1e-4 * lref
+
+
+def test_training_fits_a_smooth_target(capi, dev):
+    import torch
+    g = inputs.rng(13)
+    X = g.uniform(-1, 1, (1024, 12)).astype(np.float32)
+    T = np.stack([np.sin(2 * X[:, 0]) + X[:, 1] ** 2, X[:, 2] * X[:, 3], np.abs(X[:, 4]), X[:, 5] - X[:, 6]],
+                 axis=1).astype(np.float32)
+    M = np.ones_like(T)
+    w, hist = capi.perm_mlp_train(*[torch.from_numpy(a).to(dev) for a in (X, T, M)], DIMS, 300, 128, 3e-3, 5)
+    h = hist.cpu().numpy()
+    assert h[-1] < 0.05 * np.var(T) * 4 and h[-1] < h[0] / 5
+    # the trained weights reproduce their loss through the reference
+    lref = mlp_ref.loss(w.cpu().numpy().astype(np.float64), DIMS, X, T, M)
+    assert lref < 0.05 * np.var(T) * 4
+
+
+@pytest.mark.parametrize("kind", ["f64", "c128", "u8"])
+def test_auto_results_match_oracle(capi, dev, kind):
+    for k, (m, n) in enumerate([(3, 3), (5, 9), (9, 9), (12, 12), (14, 17)]):
+        seed = 9900 + 10 * k
+        if kind == "f64":
+            A = inputs.uniform_real(m, n, seed)
+        elif kind == "c128":
+            A = inputs.complex_gaussian(m, n, seed)
+        else:
+            A = inputs.bernoulli01(m, n, seed)
+        got = run(capi, "perm_auto", A, dev)
+        if kind == "u8":
+            assert got == oracle.subset_dp(A.astype(np.int64))
+        else:
+            close(got, oracle.glynn(A), A)
+        got_x = run(capi, "perm_auto", A, dev, dict(exhaustive=1))
+        if kind == "u8":
+            assert got_x == got
+        else:
+            close(got_x, oracle.glynn(A), A)
+
+
+def test_builtin_choice_without_model(capi, dev):
+    capi.perm_set_cost_model(None, None)
+    c, _ = capi.perm_auto_choice(to_dev(inputs.uniform_real(5, 5, 1), dev))
+    assert c == capi.PERM_CAND_COMBINATORIC
+    c, pred = capi.perm_auto_choice(to_dev(inputs.uniform_real(20, 20, 2), dev))
+    assert c == capi.PERM_CAND_GLYNN_FIXED
+    c, pred = capi.perm_auto_choice(to_dev(inputs.complex_gaussian(20, 20, 2), dev))
+    assert c == capi.PERM_CAND_GLYNN and math.isinf(pred[capi.PERM_CAND_RYSER])
+
+
+def test_ryser_partial_matches_oracle(capi, dev):
+    import torch
+    A = inputs.uniform_real(7, 11, 9950)
+    dA = to_dev(A, dev)
+    for a, b in [(0, 1 << 11), (5, 900), (1000, 2047)]:
+        out = capi.perm_ryser_partial(dA, a, b)
+        torch.cuda.synchronize(dev)
+        ref = oracle.ryser_partial(A, a, b)
+        assert abs(capi.dd_value(out) - ref) <= 1e-12 * max(1.0, abs(ref)) * 10
+
+
+def test_trained_model_gains_over_dispatch_without_it(capi, dev):
+    # the shipped model was trained on this GPU type by costmodel.main (600 timed grid
+    # cells); score it on a fresh held-out batch against exhaustive timing
+    from paper_2510_03421_gb300 import costmodel
+    w, dims, meta = costmodel.load()
+    assert dims == costmodel.DIMS
+    rule = costmodel.PaperRule()
+    rule.p = np.array(meta["paper_rule"])
+    res = costmodel.evaluate(dev, w, rule, 300, 9961)
+    r = res["ratio_to_exhaustive"]
+    print(res)
+    assert r["model"] < min(r["always_glynn"], r["builtin"], r["paper_rule"])
+    assert r["model"] < 1.25
+
+
+def test_model_installs_and_drives_perm_auto(capi, dev):
+    from paper_2510_03421_gb300 import costmodel
+    costmodel.install()
+    for A in (inputs.uniform_real(4, 4, 1), inputs.uniform_real(18, 18, 2), inputs.sparse_real(14, 14, 0.1, 3)):
+        c, pred = capi.perm_auto_choice(to_dev(A, dev))
+        assert 0 <= c < capi.PERM_NCAND and np.isfinite(pred[c]) and pred[c] == np.min(pred)
+        close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A)
+    capi.perm_set_cost_model(None, None)

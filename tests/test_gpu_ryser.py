@@ -45,3 +45,23 @@ def test_config_square16_golden(capi, dev):
     ref = float(g["ryser"][0]) + float(g["ryser"][1])
     assert abs(run(capi, "perm_ryser", A, dev) - ref) <= 1e-12 * abs(ref)
     assert abs(run(capi, "perm_glynn", A, dev) - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (7, 7), (3, 9), (8, 13), (12, 12)])
+def test_complex(capi, dev, m, n):
+    A = inputs.complex_gaussian(m, n, 6300 + 31 * m + n)
+    close(run(capi, "perm_ryser", A, dev), oracle.glynn(A), A)
+
+
+@pytest.mark.parametrize("m,n", [(5, 5), (9, 9), (4, 11), (10, 14), (16, 16)])
+def test_integer_exact(capi, dev, m, n):
+    B = inputs.bernoulli01(m, n, 6400 + 31 * m + n)
+    assert run(capi, "perm_ryser", B, dev) == oracle.subset_dp(B.astype(np.int64))
+    Z = inputs.rng(6500 + m).integers(-30, 31, (m, n)).astype(np.int64)
+    assert run(capi, "perm_ryser", Z, dev) == oracle.subset_dp(Z)
+
+
+def test_config_square26_binary_ryser(capi, dev):
+    g = read_golden("square26_01.txt")
+    A = inputs.square26_01(int(g["seed"][0]))
+    assert run(capi, "perm_ryser", A, dev) == int(g["per"][0])

@@ -343,3 +343,16 @@ def test_digits_lost_metric():
 
 def test_long_double_width_is_reported():
     assert oracle.ldbl_mant_dig() in (53, 64, 106, 113)
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (5, 5), (3, 7), (6, 9)])
+def test_ryser_gray_partial_sums_to_the_permanent(m, n):
+    # the Gray-ordered subset sum with the size weights of Eq. ryser_rectangle covers
+    # every subset once, so the full range equals the permanent (definition)
+    g = inputs.rng(150 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    full = oracle.ryser_partial(A, 0, 1 << n)
+    assert _rel(full, oracle.definition(A)) < 1e-13
+    cuts = sorted(set([0, 1 << n] + [int(c) for c in g.integers(0, 1 << n, 4)]))
+    parts = sum(oracle.ryser_partial(A, a, b) for a, b in zip(cuts, cuts[1:]))
+    assert _rel(parts, full) < 1e-13
