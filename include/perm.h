@@ -61,7 +61,7 @@ typedef enum {
 
 /* Arithmetic used by the real (PERM_F64) Glynn and Ryser sweeps. */
 typedef enum {
-  PERM_ARITH_AUTO = 0,  /* planner's choice */
+  PERM_ARITH_AUTO = 0,  /* planner's choice: FIXED for n >= 10 unless DMMA chunk starts are asked for */
   PERM_ARITH_FP64 = 1,  /* FP64 column sums updated by +-2 a_rj, FP64 products, Kahan sums */
   PERM_ARITH_FIXED = 2  /* exact 64-bit fixed-point column sums, FP64 (or wider) products */
 } perm_arith;

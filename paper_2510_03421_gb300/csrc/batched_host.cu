@@ -1,6 +1,7 @@
 // Host orchestration of perm_batched: size classes, the work lists, the per-handle
 // CUDA graph of the class kernels, and the launch-parameter tuner.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -49,11 +50,14 @@ struct Plan {
 inline int order_of(int m, int n) { return m > n ? m : n; }
 inline int rows_of(int m, int n) { return m > n ? n : m; }
 
-Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, const BatchTune& t) {
+Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, const BatchTune& t,
+                const std::vector<int32_t>* subset = nullptr) {
   Plan p;
   const int64_t count = (int64_t)M.size();
   std::vector<std::vector<int32_t>> bucket(kClasses);
-  for (int64_t b = 0; b < count; ++b) {
+  const int64_t nb = subset ? (int64_t)subset->size() : count;
+  for (int64_t q = 0; q < nb; ++q) {
+    const int64_t b = subset ? (*subset)[q] : q;
     const int n = order_of(M[b], N[b]);
     const int npad = n <= 4 ? 4 : ((n + 3) & ~3);
     const bool lane = n <= t.n_small && npad <= 16;
@@ -228,6 +232,68 @@ BatchArgs args_for(perm_handle_s* h, const Layout& L, const double* dpacked, con
   return a;
 }
 
+// Launch-parameter tuner: time the class kernels on an evenly spaced sample of the
+// batch (at most 4096 matrices) for each candidate setting and keep the fastest.
+int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vector<int32_t>& hN, int dtype,
+               const BatchArgs& base_args, size_t start, cudaStream_t s, BatchTune* best) {
+  const int64_t count = (int64_t)hM.size();
+  std::vector<int32_t> sample;
+  const int64_t stride = count > 4096 ? count / 4096 : 1;
+  for (int64_t b = 0; b < count; b += stride) sample.push_back((int32_t)b);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PERM_ECUDA;
+  float best_ms = INFINITY;
+  const int smalls[] = {6, 8, 10, 12};
+  const int items[] = {14, 16, 18};
+  const int blocks[] = {64, 128};
+  int rc = PERM_OK;
+  for (int ns : smalls)
+    for (int il : items)
+      for (int bl : blocks) {
+        BatchTune t = *best;
+        t.n_small = ns;
+        t.item_log2 = il;
+        t.block = bl;
+        Plan p = build_plan(hM, hN, t, &sample);
+        for (Plan::Cls& c : p.classes) {
+          const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+          int grid = h->sms * (bps > 0 ? bps : 1);
+          const int need = (c.nitems + t.block / 32 - 1) / (t.block / 32);
+          c.grid = need < grid ? (need > 0 ? need : 1) : grid;
+        }
+        Layout L = layout_of(p, count, start);
+        if ((rc = ensure_bws(h, L.end)) != PERM_OK) goto done;
+        if ((rc = upload_plan(h, p, L, count, s)) != PERM_OK) goto done;
+        {
+          BatchArgs a = base_args;
+          char* base = static_cast<char*>(h->bws);
+          a.order = reinterpret_cast<const int32_t*>(base + L.order);
+          a.part_base = reinterpret_cast<const int32_t*>(base + L.part_base);
+          a.partials = reinterpret_cast<double*>(base + L.partials);
+          a.done = reinterpret_cast<int*>(base + L.done);
+          a.chunk_log2 = t.chunk_log2;
+          if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;  // warm-up
+          cudaEventRecord(e0, s);
+          if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = PERM_ECUDA;
+            goto done;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            *best = t;
+          }
+        }
+      }
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 }  // namespace
 
 void batched_release(perm_handle_s* h) {
@@ -271,25 +337,27 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     return PERM_ECUDA;
   int64_t elems = 0;
   uint64_t hist = 0;
+  size_t max_parts = 0;  // sub-ranges at the finest cut the tuner tries (2^14 terms)
   for (int64_t b = 0; b < count; ++b) {
     if (hM[b] < 0 || hN[b] < 0 || hoff[b] < 0) return PERM_EINVAL;
-    if (order_of(hM[b], hN[b]) > kMaxBatchN) return PERM_ETOOBIG;
+    const int n = order_of(hM[b], hN[b]);
+    if (n > kMaxBatchN) return PERM_ETOOBIG;
     elems = std::max<int64_t>(elems, hoff[b] + (int64_t)hM[b] * hN[b]);
+    max_parts += (n > 15) ? ((size_t)1 << (n - 15)) : 1;
   }
   for (int64_t b = 0; b < count; ++b) hist = mix(hist, (uint64_t)hM[b] * 131 + hN[b]);
 
-  BatchTune t = h->tune;
+  BatchTune t = h->tuned && h->tuned_hist == hist ? h->tune : BatchTune();
   if (opts && opts->chunk_log2) t.chunk_log2 = opts->chunk_log2;
   if (opts && opts->block) {
     if (opts->block % 32 || opts->block > 128) return PERM_EINVAL;
     t.block = opts->block;
   }
 
-  // staged operands (host packed / out) live at the start of the batch workspace
+  // staged operands (host packed / out / sizes) live at the start of the batch workspace
   const bool host_packed = !on_device(packed), host_out = !on_device(out);
   const bool host_sizes = !dev_off || !dev_M || !dev_N;
-  size_t start = 0;
-  size_t packed_at = 0, out_at = 0, sizes_at = 0;
+  size_t start = 0, packed_at = 0, out_at = 0, sizes_at = 0;
   if (host_packed) {
     packed_at = start;
     start = align256(start + 8 * W * (size_t)elems);
@@ -302,18 +370,9 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     sizes_at = start;
     start = align256(start + 16 * (size_t)count);
   }
-
-  Plan p = build_plan(hM, hN, t);
-  for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
-    const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
-    const int warps_per_block = t.block / 32;
-    int grid = h->sms * (bps > 0 ? bps : 1);
-    const int need = (c.nitems + warps_per_block - 1) / warps_per_block;
-    if (need < grid) grid = need > 0 ? need : 1;
-    c.grid = grid;
-  }
-  Layout L = layout_of(p, count, start);
-  rc = ensure_bws(h, L.end);
+  // room for any plan: order, part_base, done (4 B each per matrix), items and partial slots
+  const size_t plan_bound = 12 * (size_t)count + 48 * (max_parts + (size_t)count) + 4 * kClasses + 8 * 256;
+  rc = ensure_bws(h, start + plan_bound);
   if (rc) return rc;
   char* base = static_cast<char*>(h->bws);
   const double* dpacked = static_cast<const double*>(packed);
@@ -337,6 +396,40 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     dM = reinterpret_cast<const int32_t*>(sz + 8 * count);
     dN = reinterpret_cast<const int32_t*>(sz + 12 * count);
   }
+
+  if (opts && opts->exhaustive && !(h->tuned && h->tuned_hist == hist)) {
+    // tune on a sample of this batch; kept for later batches with the same sizes
+    if (h->cache.valid) {
+      cudaGraphExecDestroy(h->cache.exec);
+      h->cache.valid = false;
+    }
+    BatchArgs probe;
+    probe.packed = dpacked;
+    probe.offsets = doff;
+    probe.M = dM;
+    probe.N = dN;
+    probe.out = dout;
+    BatchTune best = t;
+    rc = tune_batch(h, hM, hN, dtype, probe, start, s, &best);
+    if (rc) return rc;
+    if (opts->chunk_log2) best.chunk_log2 = opts->chunk_log2;
+    h->tune = best;
+    h->tuned = true;
+    h->tuned_hist = hist;
+    t = best;
+  }
+
+  Plan p = build_plan(hM, hN, t);
+  for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
+    const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+    const int warps_per_block = t.block / 32;
+    int grid = h->sms * (bps > 0 ? bps : 1);
+    const int need = (c.nitems + warps_per_block - 1) / warps_per_block;
+    if (need < grid) grid = need > 0 ? need : 1;
+    c.grid = grid;
+  }
+  Layout L = layout_of(p, count, start);
+  if (L.end > h->bws_bytes) return PERM_ENOMEM;  // cannot happen: plan_bound covers every plan
 
   uint64_t key = mix(hist, (uint64_t)count);
   key = mix(key, (uint64_t)dtype);

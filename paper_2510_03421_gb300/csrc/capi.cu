@@ -276,8 +276,12 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   return PERM_OK;
 }
 
+// Real Glynn: the integer-pipe sweep by default (faster on GB300 and at least as
+// accurate), the FP64 sweep when asked for or when the tensor-core chunk starts are.
 int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
-  if (c.o.arith == PERM_ARITH_FIXED) return glynn_fixed(c, raw, g0, g1);
+  const bool fixed = c.o.arith == PERM_ARITH_FIXED ||
+                     (c.o.arith == PERM_ARITH_AUTO && c.o.start != PERM_START_DMMA && c.n >= 10);
+  if (fixed) return glynn_fixed(c, raw, g0, g1);
   return glynn_fp64(c, raw, g0, g1);
 }
 
@@ -342,7 +346,46 @@ double binomial_d(int a, int b) {
 
 // Ryser over the 2^n column subsets (square: Eq. ryser_square; m < n: the subset-size
 // weights of Eq. ryser_rectangle).
+// Rectangular Ryser visiting only the subsets of size <= m, by size in colex order.
+int ryser_by_size(Call& c, unsigned long long total) {
+  if (total > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
+  const int block = 256;
+  int bps = ryser_colex_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, total, 16, kRealRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, total, 14);
+  SizeWeights w;
+  SizeCounts cum;
+  unsigned long long run = 0;
+  for (int s = 0; s <= 64; ++s) {
+    w.w[s] = 0.0;
+    if (s <= c.m) w.w[s] = (((c.m - s) & 1) ? -1.0 : 1.0) * binomial_d(c.n - s, c.m - s);
+  }
+  for (int s = 0; s < 66; ++s) cum.c[s] = 0;
+  for (int s = 1; s <= c.m + 1 && s < 66; ++s) {
+    cum.c[s] = run;
+    if (s <= c.m) {
+      unsigned __int128 b = 1;  // exact C(n, s)
+      for (int i = 1; i <= s; ++i) b = b * (unsigned __int128)(c.n - s + i) / (unsigned __int128)i;
+      run += (unsigned long long)b;
+    }
+  }
+  if (run != total) return PERM_ETOOBIG;
+  if (launch_ryser_colex(a, w, cum, lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, 0.0, static_cast<double*>(c.dOut),
+                         nullptr, false, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
 int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
+  if (!raw && c.m < c.n) {
+    // by size when the subsets of size <= m are few compared with all 2^n
+    long double by_size = 0.0L;
+    for (int s = 1; s <= c.m; ++s) by_size += (long double)binomial_d(c.n, s);
+    if (by_size * 3.0L < std::ldexp(1.0L, c.n) && by_size < 1.8e19L) return ryser_by_size(c, (unsigned long long)by_size);
+  }
   if (c.n > 62) return PERM_ETOOBIG;
   const uint64_t terms = raw ? g1 - g0 : (1ull << c.n);
   if (!raw) g1 = terms;

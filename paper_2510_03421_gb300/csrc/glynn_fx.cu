@@ -168,7 +168,7 @@ __device__ __forceinline__ dd acc_to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
 }
 
 template <int N, bool ABS>
-__global__ void __launch_bounds__(256) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
+__global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   extern __shared__ long long smem_fx[];
   __shared__ dd scratch[2 * 32];
   const int n = a.n;

@@ -71,6 +71,14 @@ struct SizeWeights {
   double w[65];
 };
 cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, const LaunchCfg& c, bool want_abs);
+// c[s] = number of nonempty subsets of size < s (c[1] = 0): start of size s in the
+// global index of the by-size Ryser enumeration
+struct SizeCounts {
+  unsigned long long c[66];
+};
+// rectangular Ryser by subset size in colex order (ryser_colex.cu), real FP64
+cudaError_t launch_ryser_colex(const SweepArgs& a, const SizeWeights& w, const SizeCounts& cum, const LaunchCfg& c);
+int ryser_colex_blocks_per_sm(int m, int n, int block);
 // exact weights for the integer Ryser sweep, as two's-complement int128 halves
 struct IntWeights {
   unsigned long long lo[65];

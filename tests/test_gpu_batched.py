@@ -110,3 +110,20 @@ def test_limits(capi, dev):
     with pytest.raises(capi.PermError) as e:
         capi.perm_batched(packed, offsets, M, N)
     assert e.value.status == capi.PERM_ETOOBIG
+
+
+def test_tuner_keeps_results(capi, dev):
+    import torch
+    sizes, packed, offsets = inputs.batched_haar(400, 4, 16, 9801)
+    M = sizes.astype(np.int32)
+    tp, to, tM = to_torch(dev, packed, offsets, M)
+    plain = capi.perm_batched(tp, to, tM, tM)
+    tuned = capi.perm_batched(tp, to, tM, tM, opts=dict(exhaustive=1))  # times settings on a sample
+    again = capi.perm_batched(tp, to, tM, tM)  # same sizes: the tuned setting is reused
+    torch.cuda.synchronize(dev)
+    for b in range(len(sizes)):
+        n = int(sizes[b])
+        A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
+        ref = capi.value(plain, capi.PERM_C128, b)
+        close(capi.value(tuned, capi.PERM_C128, b), ref, A)
+        assert capi.value(again, capi.PERM_C128, b) == capi.value(tuned, capi.PERM_C128, b)

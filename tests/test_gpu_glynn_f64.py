@@ -1,5 +1,5 @@
 """Parity of the real FP64 Glynn sweep (perm_glynn / perm_glynn_partial, dtype
-PERM_F64) with the CPU oracle, through the C ABI.
+PERM_F64, opts.arith = PERM_ARITH_FP64) with the CPU oracle, through the C ABI.
 
 Tolerance: relative 1e-12 for well-conditioned random inputs; for inputs whose
 terms cancel heavily the bound is the usual first-order one, 8 (n+2) u times the
@@ -36,9 +36,12 @@ def to_dev(A, dev):
     return torch.from_numpy(np.ascontiguousarray(A)).to(dev)
 
 
+FP64 = dict(arith=1)
+
+
 def glynn(capi, A, dev, opts=None):
     import torch
-    out = capi.perm_glynn(to_dev(A, dev), opts=opts)
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(FP64, **(opts or {})))
     torch.cuda.synchronize(dev)
     return capi.value(out, capi.PERM_F64)
 
@@ -94,7 +97,7 @@ def test_ones_and_identity_closed_forms(capi, dev, n):
 def test_host_buffers_match_device(capi, dev):
     A = inputs.uniform_real(14, 14, 3101)
     host_out = np.zeros(1)
-    capi.perm_glynn(A, out=host_out)
+    capi.perm_glynn(A, out=host_out, opts=FP64)
     assert host_out[0] == glynn(capi, A, dev)
 
 
@@ -118,7 +121,7 @@ def test_partial_ranges_match_oracle(capi, dev):
     g = inputs.rng(3402)
     cuts = sorted(set([0, T, 1, T - 1] + [int(c) for c in g.integers(0, T, 6)]))
     for a, b in zip(cuts, cuts[1:]):
-        out = capi.perm_glynn_partial(dA, a, b, opts=dict(chunk_log2=3))
+        out = capi.perm_glynn_partial(dA, a, b, opts=dict(FP64, chunk_log2=3))
         torch.cuda.synchronize(dev)
         got = capi.dd_value(out)
         ref = oracle.glynn_partial(A, a, b)
@@ -130,7 +133,7 @@ def test_error_bound_holds(capi, dev):
     import torch
     A = inputs.uniform_real(17, 17, 3501)
     err = torch.zeros(1, dtype=torch.float64, device=dev)
-    out = capi.perm_glynn(to_dev(A, dev), opts=dict(err=err))
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(FP64, err=err))
     torch.cuda.synchronize(dev)
     got, ref = capi.value(out, capi.PERM_F64), oracle.glynn(A)
     assert abs(got - ref) <= float(err.item())
@@ -153,7 +156,7 @@ def test_config_square36_sampled_ranges(capi, dev, where):
     T = 1 << 35
     span = 1 << 12
     a = {"start": 0, "middle": T // 2 - span // 2 + 12345, "end": T - span}[where]
-    out = capi.perm_glynn_partial(to_dev(A, dev), a, a + span, opts=dict(chunk_log2=10))
+    out = capi.perm_glynn_partial(to_dev(A, dev), a, a + span, opts=dict(FP64, chunk_log2=10))
     torch.cuda.synchronize(dev)
     got = capi.dd_value(out)
     ref = oracle.glynn_partial(A, a, a + span)
@@ -162,3 +165,14 @@ def test_config_square36_sampled_ranges(capi, dev, where):
     # column sums over at most 2^10 incremental updates between exact rebuilds
     assert abs(got - ref) <= max(1e-12 * abs(ref), (36 + 4 + 2 * 36 * 2 ** 10) * U * scale)
     assert abs(got - ref) <= 1e-11 * scale
+
+
+def test_default_arithmetic_is_the_integer_pipe_sweep(capi, dev):
+    # with no options a real matrix of order >= 10 takes the integer-pipe sweep; it
+    # agrees with the FP64 sweep and the oracle
+    import torch
+    A = inputs.uniform_real(20, 20, 3601)
+    out = capi.perm_glynn(to_dev(A, dev))
+    torch.cuda.synchronize(dev)
+    close(capi.value(out, capi.PERM_F64), oracle.glynn(A), A)
+    close(capi.value(out, capi.PERM_F64), glynn(capi, A, dev), A)

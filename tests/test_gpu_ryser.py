@@ -65,3 +65,13 @@ def test_config_square26_binary_ryser(capi, dev):
     g = read_golden("square26_01.txt")
     A = inputs.square26_01(int(g["seed"][0]))
     assert run(capi, "perm_ryser", A, dev) == int(g["per"][0])
+
+
+@pytest.mark.parametrize("m,n", [(1, 12), (2, 20), (3, 16), (4, 22), (6, 24), (2, 40)])
+def test_rectangular_by_size(capi, dev, m, n):
+    # m << n: perm_ryser visits only the subsets of size <= m (colex order per size)
+    A = inputs.uniform_real(m, n, 6600 + 31 * m + n)
+    ref = oracle.ryser_rect(A)  # the appendix algorithm: combinations of each size
+    close(run(capi, "perm_ryser", A, dev), ref, A)
+    close(run(capi, "perm_ryser", A, dev, dict(chunk_log2=3)), ref, A)
+    close(run(capi, "perm_ryser", np.ascontiguousarray(A.T), dev), ref, A)
