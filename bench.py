@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=36, help="matrix order (36 is the benchmark workload)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "c128"],
+                    help="c128: the 32x32 complex workload (profiling runs)")
     ap.add_argument("--arith", default="auto", choices=["auto", "fp64", "fixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 100,000-matrix leg")
@@ -48,8 +50,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n: int):
+def workload(n: int, dtype: str = "f64"):
     from paper_2510_03421_gb300 import inputs
+    if dtype == "c128":
+        A = inputs.complex_gaussian(n, n, inputs.SEED_BASE + 2)
+        return A, "glynn %dx%d complex128 Gaussian/sqrt(n) seed %d (2^%d Gray-code terms per step)" % (
+            n, n, inputs.SEED_BASE + 2, n - 1)
     if n == 36:
         A = inputs.square36_f64()
     else:
@@ -234,12 +240,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2510_03421_gb300 import capi
 
-    A, desc = workload(args.n)
+    A, desc = workload(args.n, args.dtype)
     n = args.n
     terms = 1 << (n - 1)
     arith = {"auto": capi.PERM_ARITH_AUTO, "fp64": capi.PERM_ARITH_FP64, "fixed": capi.PERM_ARITH_FIXED}[args.arith]
     dA = torch.from_numpy(A).to(dev)
-    out = torch.empty(1, dtype=torch.float64, device=dev)
+    out = torch.empty(2 if args.dtype == "c128" else 1, dtype=torch.float64, device=dev)
     err = torch.empty(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     opts = capi.perm_opts(arith=arith)
@@ -252,9 +258,14 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         capi.perm_glynn(dA, out=out, stream=stream, opts=opts)
-    capi.perm_glynn(dA, out=out, stream=stream, opts=opts_err)  # result and its stated error bound
-    torch.cuda.synchronize(dev)
-    result, err_bound = float(out.item()), float(err.item())
+    if args.dtype == "c128":  # the complex integer-pipe sweep states no bound
+        capi.perm_glynn(dA, out=out, stream=stream, opts=opts)
+        torch.cuda.synchronize(dev)
+        result, err_bound = [float(v) for v in out.cpu()], None
+    else:
+        capi.perm_glynn(dA, out=out, stream=stream, opts=opts_err)  # result and its stated error bound
+        torch.cuda.synchronize(dev)
+        result, err_bound = float(out.item()), float(err.item())
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -280,7 +291,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host (pinned) buffers, copies inside the timed region
     hA = torch.from_numpy(A).pin_memory()
-    hout = torch.empty(1, dtype=torch.float64).pin_memory()
+    hout = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -318,11 +329,15 @@ def run_ours(args):
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
         "result": result, "err_bound": err_bound,
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.nbytes), "d2h_bytes_per_step": 8},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.nbytes),
+                "d2h_bytes_per_step": 8 * out.numel()},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks.summary(),
     }
-    if fixed and not args.no_fp64:
+    if args.dtype == "c128":
+        line["dtype"] = "c128"
+        line["roofline"] = None  # complex runs are profiling runs; the headline is the real workload
+    if fixed and not args.no_fp64 and args.dtype == "f64":
         # the plain FP64 sweep on the same matrix, for comparison at stated error
         o64 = capi.perm_opts(arith=capi.PERM_ARITH_FP64)
         o64e = capi.perm_opts(arith=capi.PERM_ARITH_FP64, err=err.data_ptr())

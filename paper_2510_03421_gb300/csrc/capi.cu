@@ -174,7 +174,11 @@ int* call_status_word(perm_handle h) { return reinterpret_cast<int*>(static_cast
 
 // workspace layout: [staged operand | result/err/status | fixed-point table | partial records]
 constexpr size_t kFxTableOffset = kStageA + kStageOut * 16;
-constexpr size_t kPartialsOffset = kFxTableOffset + ((sizeof(FxTable) + 255) / 256) * 256;
+constexpr size_t kCfxTableOffset = kFxTableOffset + ((sizeof(FxTable) + 255) / 256) * 256;
+constexpr size_t kPartialsOffset = kCfxTableOffset + ((sizeof(CfxTable) + 255) / 256) * 256;
+CfxTable* cfx_table(perm_handle h) {
+  return reinterpret_cast<CfxTable*>(static_cast<char*>(h->ws) + kCfxTableOffset);
+}
 FxTable* fx_table(perm_handle h) { return reinterpret_cast<FxTable*>(static_cast<char*>(h->ws) + kFxTableOffset); }
 char* partials_base(perm_handle h) { return static_cast<char*>(h->ws) + kPartialsOffset; }
 size_t partials_capacity(perm_handle h) { return h->ws_bytes - kPartialsOffset; }
@@ -263,9 +267,15 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   int bps = glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
   lc.stream = c.stream;
-  // the 192-bit accumulator holds up to 2^40 maximal terms per thread
-  if ((g1 - g0) / ((uint64_t)lc.grid * lc.block) >= (1ull << 40)) return PERM_ETOOBIG;
-  SweepArgs a = sweep_args(c, g0, g1, 62);
+  SweepArgs a = sweep_args(c, g0, g1, 12);
+  if (!c.o.chunk_log2) {
+    // aligned chunks of 2^k terms, at least 32 rounds of 32 chunks per resident warp
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 12;
+    while (k > 2 && ((g1 - g0) >> k) < 1024 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  if (a.chunk_log2 > 40) return PERM_ETOOBIG;  // the 192-bit accumulator holds 2^40 maximal terms per chunk
   if (launch_glynn_fx(a, fx_table(c.h), lc, want_abs) != cudaSuccess) return PERM_ECUDA;
   // products: n truncations of < 2^-62 each; quantisation of A: < 2^-62 of each column's
   // absolute sum; both taken relative to sum |t|
@@ -296,11 +306,32 @@ SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk)
   a.g_end = g1;
   a.chunk_log2 = c.o.chunk_log2 ? c.o.chunk_log2 : default_chunk;
   a.start_mode = c.o.start ? c.o.start : PERM_START_SCALAR;
+  a.want_abs = 0;
   a.partials = partials_base(c.h);
   return a;
 }
 
+// Complex Glynn on the integer pipes (glynn_cfx.cu).
+int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.o.block > 128) return PERM_EINVAL;
+  const int block = 128;
+  int bps = glynn_cfx_blocks_per_sm(c.n, c.o.block ? c.o.block : block);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kCplxRecord * sizeof(double));
+  lc.stream = c.stream;
+  if ((g1 - g0) / ((uint64_t)lc.grid * lc.block) >= (1ull << 40)) return PERM_ETOOBIG;
+  SweepArgs a = sweep_args(c, g0, g1, 62);
+  if (launch_glynn_cfx(a, cfx_table(c.h), lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, 0.0,
+                         static_cast<double*>(c.dOut), nullptr, raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
 int glynn_cplx(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  const bool fixed = c.n <= glynn_cfx_max_n() && !c.dErr &&
+                     (c.o.arith == PERM_ARITH_FIXED || (c.o.arith == PERM_ARITH_AUTO && c.n >= 10));
+  if (fixed) return glynn_cfixed(c, raw, g0, g1);
   if (c.n > glynn_c128_max_n()) return PERM_ETOOBIG;
   if (c.o.block > 128) return PERM_EINVAL;
   const bool want_abs = c.dErr != nullptr;

@@ -1,0 +1,306 @@
+// Glynn's formula (Eq. glynn, Eq. glynn_rectangle) for complex input on the integer
+// pipes, the complex counterpart of glynn_fx.cu:
+//   * column j is held in fixed point with its own scale 2^e_j, chosen so that
+//     sum_i (|re a'_ij| + |im a'_ij|) 2^e_j <= 2^61; real and imaginary parts are
+//     rounded once to int64, and the +-2q updates of the walk are exact;
+//   * the running product is a complex software float: two signed 64-bit mantissas
+//     (re, im) with one shared exponent, the larger magnitude kept in [2^61, 2^62).
+//     Each factor is normalised the same way, the four partial products are the high
+//     halves of signed 64x64-bit products (truncation error < 2^-60 of the larger
+//     component), and the result is renormalised by clz of the larger component;
+//   * the signed terms go into two 192-bit fixed-point accumulators (re, im) sharing a
+//     window anchored on the thread's first nonzero term, moved up if a later term
+//     would overflow it.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace perm {
+namespace {
+
+typedef unsigned long long u64;
+
+constexpr int kAnchorBit = 120;
+constexpr int kMaxLsb = 87;
+
+// One block, one thread per column: scales and the quantised +-2q table (re, im).
+__global__ void cfx_prep_kernel(SweepArgs a, CfxTable* tab) {
+  const int n = a.n, m = a.m;
+  const double* A = static_cast<const double*>(a.A);
+  __shared__ int es[64];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < n) {
+    double colabs = (double)(n - m);
+    for (int i = 0; i < m; ++i) {
+      const int64_t e = 2 * (i * a.rs + j * a.cs);
+      if (!isfinite(A[e]) || !isfinite(A[e + 1])) bad = 1;
+      colabs += fabs(A[e]) + fabs(A[e + 1]);
+    }
+    int x = 0;
+    if (colabs > 0.0) frexp(colabs, &x);
+    const int e = 61 - x;
+    es[j] = e;
+    for (int i = 0; i < n; ++i) {
+      long long qr = 0, qi = 0;
+      if (i < m) {
+        const int64_t el = 2 * (i * a.rs + j * a.cs);
+        qr = llrint(ldexp(A[el], e));
+        qi = llrint(ldexp(A[el + 1], e));
+      } else {
+        qr = llrint(ldexp(1.0, e));
+      }
+      tab->d[2 * (i * 64 + j)] = 2 * qr;
+      tab->d[2 * (i * 64 + j) + 1] = 2 * qi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int esum = 0;
+    for (int k = 0; k < n; ++k) esum += es[k];
+    tab->e_sum = esum;
+    tab->bad = bad;
+  }
+}
+
+__device__ __forceinline__ u64 uabs(long long v) { return v < 0 ? (u64)(-v) : (u64)v; }
+
+// Shift count that brings max(|x|, |y|) into [2^61, 2^62) (0 if both are zero).
+__device__ __forceinline__ int norm_shift(long long x, long long y) {
+  const u64 mx = uabs(x) | uabs(y);  // same leading bit as the max
+  return (__clzll((long long)mx) - 2) & 63;
+}
+
+// (pr + i pi) 2^(E - 62) is the product of the factors so far (column scales excluded).
+template <int N>
+__device__ __forceinline__ void soft_cproduct(const long long (&Sr)[N], const long long (&Si)[N], long long& pr,
+                                              long long& pi, int& E) {
+  {
+    const int l = norm_shift(Sr[0], Si[0]);
+    pr = Sr[0] << l;
+    pi = Si[0] << l;
+    E = 62 - l;
+  }
+#pragma unroll
+  for (int j = 1; j < N; ++j) {
+    const int l = norm_shift(Sr[j], Si[j]);
+    const long long sr = Sr[j] << l, si = Si[j] << l;
+    const long long re = __mul64hi(pr, sr) - __mul64hi(pi, si);
+    const long long im = __mul64hi(pr, si) + __mul64hi(pi, sr);
+    const int l2 = norm_shift(re, im);
+    pr = re << l2;
+    pi = im << l2;
+    E += 64 - l - l2;
+  }
+}
+
+__device__ __forceinline__ void add192(u64& a0, u64& a1, u64& a2, long long v, int p) {
+  // a += v * 2^p for a signed 64-bit v (|v| < 2^62), p <= kMaxLsb
+  const bool neg = v < 0;
+  const u64 P = neg ? (u64)(-v) : (u64)v;
+  u64 t0, t1, t2;
+  if (p >= 64) {
+    const int q = p - 64;
+    t0 = 0;
+    t1 = P << q;
+    t2 = q ? (P >> (64 - q)) : 0;
+  } else if (p >= 0) {
+    t0 = P << p;
+    t1 = p ? (P >> (64 - p)) : 0;
+    t2 = 0;
+  } else if (p > -64) {
+    t0 = P >> (-p);
+    t1 = 0;
+    t2 = 0;
+  } else {
+    t0 = t1 = t2 = 0;
+  }
+  if (neg) {
+    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+        : "+l"(a0), "+l"(a1), "+l"(a2)
+        : "l"(t0), "l"(t1), "l"(t2));
+  } else {
+    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+        : "+l"(a0), "+l"(a1), "+l"(a2)
+        : "l"(t0), "l"(t1), "l"(t2));
+  }
+}
+
+__device__ __forceinline__ void shr192(u64& a0, u64& a1, u64& a2, int s) {
+  const u64 sgn = (u64)((long long)a2 >> 63);
+  while (s >= 64) {
+    a0 = a1;
+    a1 = a2;
+    a2 = sgn;
+    s -= 64;
+  }
+  if (s > 0) {
+    a0 = (a0 >> s) | (a1 << (64 - s));
+    a1 = (a1 >> s) | (a2 << (64 - s));
+    a2 = (u64)((long long)a2 >> s);
+  }
+}
+
+__device__ __forceinline__ dd to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
+  const bool negative = (long long)a2 < 0;
+  if (negative) {
+    asm("sub.cc.u64 %0, 0, %0;\n\tsubc.cc.u64 %1, 0, %1;\n\tsubc.u64 %2, 0, %2;" : "+l"(a0), "+l"(a1), "+l"(a2));
+  }
+  const u64 mask = (1ull << 48) - 1;
+  dd r = dd{scalbn((double)(a2 >> 16), e_lo + 144), 0.0};
+  r = dd_add(r, dd{scalbn((double)(((a1 >> 32) | (a2 << 32)) & mask), e_lo + 96), 0.0});
+  r = dd_add(r, dd{scalbn((double)(((a0 >> 48) | (a1 << 16)) & mask), e_lo + 48), 0.0});
+  r = dd_add(r, dd{scalbn((double)(a0 & mask), e_lo), 0.0});
+  if (negative) {
+    r.hi = -r.hi;
+    r.lo = -r.lo;
+  }
+  return r;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTable* __restrict__ tab) {
+  extern __shared__ long long smem_cfx[];
+  __shared__ dd scratch[3 * 32];
+  const int n = a.n;
+  long long* sP = smem_cfx;              // +2q (re, im interleaved)
+  long long* sM = smem_cfx + 2 * n * N;  // -2q
+  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    const long long vr = (j < n) ? tab->d[2 * (i * 64 + j)] : 0;
+    const long long vi = (j < n) ? tab->d[2 * (i * 64 + j) + 1] : 0;
+    sP[2 * idx] = vr;
+    sP[2 * idx + 1] = vi;
+    sM[2 * idx] = -vr;
+    sM[2 * idx + 1] = -vi;
+  }
+  const int e_sum = tab->e_sum;
+  __syncthreads();
+
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t g, len;
+  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+
+  int e_lo = 0;
+  bool anchored = false;
+  u64 r0 = 0, r1 = 0, r2 = 0, i0 = 0, i1 = 0, i2 = 0;
+  long long Sr[N], Si[N];
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) Sr[j] = Si[j] = 0;
+      for (int i = 0; i < n; ++i) {
+        const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + 2 * i * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          Sr[j] += row[2 * j];
+          Si[j] += row[2 * j + 1];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Sr[j] = (j < n) ? (Sr[j] >> 1) : 1ll;
+        Si[j] = (j < n) ? (Si[j] >> 1) : 0ll;
+      }
+    } else {
+      const int b = ctz64(g);
+      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + 2 * (n - 1 - b) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Sr[j] += row[2 * j];
+        Si[j] += row[2 * j + 1];
+      }
+    }
+    long long pr, pi;
+    int E;
+    soft_cproduct(Sr, Si, pr, pi, E);
+    if (pr != 0 || pi != 0) {
+      if (g & 1u) {
+        pr = -pr;
+        pi = -pi;
+      }
+      if (!anchored) {
+        e_lo = E - e_sum - kAnchorBit - 1;
+        anchored = true;
+      }
+      // a component's lsb has weight 2^(E - 62 - e_sum): bit p of the accumulators
+      int p = E - 62 - e_sum - e_lo;
+      if (p > kMaxLsb) {
+        shr192(r0, r1, r2, p - kMaxLsb);
+        shr192(i0, i1, i2, p - kMaxLsb);
+        e_lo += p - kMaxLsb;
+        p = kMaxLsb;
+      }
+      add192(r0, r1, r2, pr, p);
+      add192(i0, i1, i2, pi, p);
+    }
+  }
+
+  dd v[3] = {to_dd(r0, r1, r2, e_lo), to_dd(i0, i1, i2, e_lo), dd{0.0, 0.0}};
+  block_sum_dd<3>(v, scratch);
+  if (threadIdx.x == 0) {
+    const bool bad = tab->bad != 0;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kCplxRecord;
+    rec[0] = bad ? nan : v[0].hi;
+    rec[1] = bad ? 0.0 : v[0].lo;
+    rec[2] = bad ? nan : v[1].hi;
+    rec[3] = bad ? 0.0 : v[1].lo;
+    rec[4] = 0.0;
+    rec[5] = 0.0;
+  }
+}
+
+void* pick(int n) {
+  switch ((n + 3) & ~3) {
+    case 4: return (void*)glynn_cfx_kernel<4>;
+    case 8: return (void*)glynn_cfx_kernel<8>;
+    case 12: return (void*)glynn_cfx_kernel<12>;
+    case 16: return (void*)glynn_cfx_kernel<16>;
+    case 20: return (void*)glynn_cfx_kernel<20>;
+    case 24: return (void*)glynn_cfx_kernel<24>;
+    case 28: return (void*)glynn_cfx_kernel<28>;
+    case 32: return (void*)glynn_cfx_kernel<32>;
+    case 36: return (void*)glynn_cfx_kernel<36>;
+    case 40: return (void*)glynn_cfx_kernel<40>;
+    default: return nullptr;
+  }
+}
+
+size_t smem_bytes(int n) { return 4u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long); }
+
+}  // namespace
+
+int glynn_cfx_max_n() { return 40; }
+
+int glynn_cfx_blocks_per_sm(int n, int block) {
+  void* k = pick(n);
+  if (!k) return 0;
+  size_t smem = smem_bytes(n);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg& c) {
+  void* k = pick(a.n);
+  if (!k) return cudaErrorInvalidValue;
+  cfx_prep_kernel<<<1, 64, 0, c.stream>>>(a, tab);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t smem = smem_bytes(a.n);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  SweepArgs args = a;
+  const CfxTable* tp = tab;
+  void* params[] = {&args, &tp};
+  return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
+}
+
+}  // namespace perm

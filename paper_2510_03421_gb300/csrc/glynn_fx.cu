@@ -74,28 +74,38 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
 }
 
 // value = sign * P * 2^(E - 63) * 2^(-e_sum), P in [2^63, 2^64); P == 0 iff some
-// factor is zero (a zero factor gives a zero high half, which stays zero)
+// factor is zero.  Columns are taken in pairs: the product of two column sums
+// (each below 2^62 in magnitude) is formed exactly in 128 bits, its leading 64 bits
+// are multiplied into P with the high half of a 64x64-bit product (truncation error
+// < 2^-62 per pair), and P is renormalised by at most one bit.
 template <int N>
 __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, int& E, unsigned& neg) {
-  {
-    const long long q = S[0];
-    neg = (unsigned)((u64)q >> 63);
-    const u64 aq = (q < 0) ? (u64)(-q) : (u64)q;
-    const int lz = __clzll((long long)aq) & 63;
-    P = aq << lz;
-    E = 63 - lz;
-  }
+  static_assert(N % 2 == 0, "columns are padded to an even count");
+  P = 1ull << 63;  // the value 1
+  E = 0;
+  neg = 0;
 #pragma unroll
-  for (int j = 1; j < N; ++j) {
-    const long long q = S[j];
-    neg ^= (unsigned)((u64)q >> 63);
-    const u64 aq = (q < 0) ? (u64)(-q) : (u64)q;
-    const int lz = __clzll((long long)aq) & 63;
-    const u64 mj = aq << lz;
-    const u64 hi = __umul64hi(P, mj);  // truncated high half: error < 2^-62 relative
-    const int top = (int)(hi >> 63);
-    P = top ? hi : (hi << 1);
-    E += (63 - lz) + top;
+  for (int j = 0; j < N; j += 2) {
+    const long long qa = S[j], qb = S[j + 1];
+    neg ^= (unsigned)((u64)(qa ^ qb) >> 63);
+    const u64 aa = (qa < 0) ? (u64)(-qa) : (u64)qa;
+    const u64 ab = (qb < 0) ? (u64)(-qb) : (u64)qb;
+    const u64 hi = __umul64hi(aa, ab), lo = aa * ab;
+    u64 mc;
+    int ec;  // the pair product is mc * 2^(ec - 64), mc normalised (or 0)
+    if (hi != 0) {
+      const int lz = __clzll((long long)hi);  // >= 4: both factors are below 2^62
+      mc = (hi << lz) | (lo >> (64 - lz));
+      ec = 128 - lz;
+    } else {
+      const int lz = __clzll((long long)lo) & 63;
+      mc = lo << lz;
+      ec = 64 - lz;
+    }
+    const u64 h2 = __umul64hi(P, mc);
+    const int top = (int)(h2 >> 63);
+    P = top ? h2 : (h2 << 1);
+    E += ec - 1 + top;
   }
 }
 
@@ -167,8 +177,9 @@ __device__ __forceinline__ dd acc_to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
   return r;
 }
 
-template <int N, bool ABS>
+template <int N>
 __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
+  const bool ABS = a.want_abs != 0;
   extern __shared__ long long smem_fx[];
   __shared__ dd scratch[2 * 32];
   const int n = a.n;
@@ -183,10 +194,17 @@ __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
   const int e_sum = tab->e_sum;
   __syncthreads();
 
-  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t g, len;
-  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+  // Work: chunks of L = 2^chunk_log2 terms aligned to multiples of L; a warp takes 32
+  // consecutive chunks at a time, one per lane, so all lanes flip the same row at the
+  // same step (the table row is read as a broadcast).  Edge chunks are clipped to
+  // [g_begin, g_end).
+  const int lane = threadIdx.x & 31;
+  const uint64_t L = 1ull << a.chunk_log2;
+  const uint64_t c_first = a.g_begin >> a.chunk_log2;
+  const uint64_t c_end = (a.g_end + L - 1) >> a.chunk_log2;
+  const uint64_t rounds = (c_end - c_first + 31) / 32;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
 
   // value of a term with mantissa P, exponent E: P * 2^(E - 63 - e_sum); its lsb sits
   // at accumulator bit p = E - 63 - e_sum - e_lo
@@ -195,43 +213,50 @@ __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
   u64 a0 = 0, a1 = 0, a2 = 0;
   u64 b0 = 0, b1 = 0, b2 = 0;  // sum of |term| (ABS only)
   long long S[N];
-  for (uint64_t s = 0; s < len; ++s, ++g) {
-    if (s == 0) {
-      const uint64_t gray = g ^ (g >> 1);
+  for (uint64_t r = warp; r < rounds; r += warps) {
+    const uint64_t chunk = c_first + 32 * r + lane;
+    uint64_t ga = chunk << a.chunk_log2, gb = ga + L;
+    if (ga < a.g_begin) ga = a.g_begin;
+    if (gb > a.g_end) gb = a.g_end;
+    if (chunk >= c_end) ga = gb = a.g_end;  // idle lane
+    for (uint64_t g = ga; g < gb; ++g) {
+      if (g == ga) {
+        const uint64_t gray = g ^ (g >> 1);
 #pragma unroll
-      for (int j = 0; j < N; ++j) S[j] = 0;
-      for (int i = 0; i < n; ++i) {
-        const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + i * N;
+        for (int j = 0; j < N; ++j) S[j] = 0;
+        for (int i = 0; i < n; ++i) {
+          const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + i * N;
+#pragma unroll
+          for (int j = 0; j < N; ++j) S[j] += row[j];
+        }
+        // padded columns hold the constant 1 (scale 2^0, not part of e_sum)
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] >> 1) : 1ll;
+      } else {
+        const int b = ctz64(g);
+        const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N;
 #pragma unroll
         for (int j = 0; j < N; ++j) S[j] += row[j];
       }
-      // padded columns hold the constant 1 (scale 2^0, not part of e_sum)
-#pragma unroll
-      for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] >> 1) : 1ll;
-    } else {
-      const int b = ctz64(g);
-      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) S[j] += row[j];
-    }
-    u64 P;
-    int E;
-    unsigned neg;
-    soft_product(S, P, E, neg);
-    if (P != 0) {
-      if (!anchored) {
-        e_lo = E - e_sum - kAnchorBit;
-        anchored = true;
+      u64 P;
+      int E;
+      unsigned neg;
+      soft_product(S, P, E, neg);
+      if (P != 0) {
+        if (!anchored) {
+          e_lo = E - e_sum - kAnchorBit;
+          anchored = true;
+        }
+        int p = E - 63 - e_sum - e_lo;
+        if (p > kMaxLsb) {  // rare: move the window up
+          shr192(a0, a1, a2, p - kMaxLsb);
+          if (ABS) shr192(b0, b1, b2, p - kMaxLsb);
+          e_lo += p - kMaxLsb;
+          p = kMaxLsb;
+        }
+        acc_add(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u));
+        if (ABS) acc_add(b0, b1, b2, P, p, 0u);
       }
-      int p = E - 63 - e_sum - e_lo;
-      if (p > kMaxLsb) {  // rare: move the window up
-        shr192(a0, a1, a2, p - kMaxLsb);
-        if (ABS) shr192(b0, b1, b2, p - kMaxLsb);
-        e_lo += p - kMaxLsb;
-        p = kMaxLsb;
-      }
-      acc_add(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u));
-      if (ABS) acc_add(b0, b1, b2, P, p, 0u);
     }
   }
 
@@ -248,8 +273,8 @@ __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
 }
 
 template <int N>
-void* kernel_for(bool abs) {
-  return abs ? (void*)glynn_fx_kernel<N, true> : (void*)glynn_fx_kernel<N, false>;
+void* kernel_for(bool) {
+  return (void*)glynn_fx_kernel<N>;
 }
 
 void* pick(int n, bool abs) {
@@ -300,6 +325,7 @@ cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c
     if (e != cudaSuccess) return e;
   }
   SweepArgs args = a;
+  args.want_abs = want_abs ? 1 : 0;
   const FxTable* tp = tab;
   void* params[] = {&args, &tp};
   return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);

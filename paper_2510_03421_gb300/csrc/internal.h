@@ -15,6 +15,7 @@ struct SweepArgs {
   uint64_t g_end;     // one past the last term
   int chunk_log2;     // column sums are rebuilt exactly at every multiple of 2^chunk_log2
   int start_mode;     // 1 = per-thread rebuild, 2 = warp DMMA contraction
+  int want_abs;       // integer-pipe sweeps: also accumulate sum |term| (runtime flag)
   void* partials;     // per-block records (layout per kernel family, see below)
 };
 
@@ -52,6 +53,16 @@ struct FxTable {
 };
 cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
 int glynn_fx_blocks_per_sm(int n, int block, bool want_abs);
+
+// --- Glynn, complex input on the integer pipes (glynn_cfx.cu); n <= glynn_cfx_max_n()
+struct CfxTable {
+  long long d[2 * 64 * 64];  // (re, im) of +2q for row i, column j at 2 (i * 64 + j)
+  int e_sum;
+  int bad;
+};
+cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg& c);
+int glynn_cfx_blocks_per_sm(int n, int block);
+int glynn_cfx_max_n();
 
 // --- Glynn, complex FP64 (glynn_c128.cu); n <= glynn_c128_max_n()
 cudaError_t launch_glynn_c128(const SweepArgs& a, const LaunchCfg& c, bool want_abs);

@@ -123,3 +123,25 @@ def test_config_square26_binary_golden(capi, dev):
     g = read_golden("square26_01.txt")
     A = inputs.square26_01(int(g["seed"][0]))
     assert run(capi, "perm_glynn", A, dev) == int(g["per"][0])
+
+
+@pytest.mark.parametrize("m,n", [(3, 3), (6, 6), (10, 10), (13, 13), (16, 16), (7, 12), (11, 18)])
+def test_complex_integer_pipes(capi, dev, m, n):
+    # opts.arith = PERM_ARITH_FIXED: fixed-point column sums and a complex software float
+    A = inputs.complex_gaussian(m, n, 4500 + 31 * m + n)
+    ref = oracle.glynn(A)
+    close(run(capi, "perm_glynn", A, dev, dict(arith=2)), ref, A)
+    close(run(capi, "perm_glynn", A, dev, dict(arith=1)), ref, A)
+
+
+def test_complex_integer_pipes_haar_and_partial(capi, dev):
+    import torch
+    A = inputs.haar_unitary_block(14, 4601)
+    close(run(capi, "perm_glynn", A, dev, dict(arith=2)), oracle.glynn(A), A)
+    B = inputs.complex_gaussian(11, 11, 4602)
+    out = capi.perm_glynn_partial(to_dev(B, dev), 100, 900, opts=dict(arith=2))
+    torch.cuda.synchronize(dev)
+    o = out.cpu().numpy()
+    got = complex(o[0] + o[1], o[2] + o[3])
+    ref = oracle.glynn_partial(B, 100, 900)
+    assert abs(got - ref) <= 1e-12 * 800 * max(1.0, abs(ref))
