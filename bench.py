@@ -233,11 +233,11 @@ def run_ours(args):
     import torch
 
     world, rank, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so each rank's NCCL uses its own GPU
+    dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+        dist.init_process_group("nccl", device_id=dev)
     from paper_2510_03421_gb300 import capi
 
     A, desc = workload(args.n, args.dtype)

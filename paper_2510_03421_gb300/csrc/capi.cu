@@ -263,7 +263,8 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
 // products, 192-bit accumulation (glynn_fx.cu).
 int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   const bool want_abs = c.dErr != nullptr;
-  const int block = 256;
+  const int block = 192;  // 6 warps; two blocks per SM at up to 170 registers
+  if (c.o.block > 192) return PERM_EINVAL;
   int bps = glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
   lc.stream = c.stream;
@@ -314,12 +315,18 @@ SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk)
 // Complex Glynn on the integer pipes (glynn_cfx.cu).
 int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   if (c.o.block > 128) return PERM_EINVAL;
-  const int block = 128;
+  const int block = c.n <= 40 ? 128 : 64;  // shared memory: 32 n^2 + 16 n per thread bytes
   int bps = glynn_cfx_blocks_per_sm(c.n, c.o.block ? c.o.block : block);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kCplxRecord * sizeof(double));
   lc.stream = c.stream;
-  if ((g1 - g0) / ((uint64_t)lc.grid * lc.block) >= (1ull << 40)) return PERM_ETOOBIG;
-  SweepArgs a = sweep_args(c, g0, g1, 62);
+  SweepArgs a = sweep_args(c, g0, g1, 12);
+  if (!c.o.chunk_log2) {
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 12;
+    while (k > 2 && ((g1 - g0) >> k) < 1024 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  if (a.chunk_log2 > 40) return PERM_ETOOBIG;  // 2^40 maximal terms per 192-bit accumulator
   if (launch_glynn_cfx(a, cfx_table(c.h), lc) != cudaSuccess) return PERM_ECUDA;
   if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, 0.0,

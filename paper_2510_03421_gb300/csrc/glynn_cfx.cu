@@ -73,28 +73,6 @@ __device__ __forceinline__ int norm_shift(long long x, long long y) {
 }
 
 // (pr + i pi) 2^(E - 62) is the product of the factors so far (column scales excluded).
-template <int N>
-__device__ __forceinline__ void soft_cproduct(const long long (&Sr)[N], const long long (&Si)[N], long long& pr,
-                                              long long& pi, int& E) {
-  {
-    const int l = norm_shift(Sr[0], Si[0]);
-    pr = Sr[0] << l;
-    pi = Si[0] << l;
-    E = 62 - l;
-  }
-#pragma unroll
-  for (int j = 1; j < N; ++j) {
-    const int l = norm_shift(Sr[j], Si[j]);
-    const long long sr = Sr[j] << l, si = Si[j] << l;
-    const long long re = __mul64hi(pr, sr) - __mul64hi(pi, si);
-    const long long im = __mul64hi(pr, si) + __mul64hi(pi, sr);
-    const int l2 = norm_shift(re, im);
-    pr = re << l2;
-    pi = im << l2;
-    E += 64 - l - l2;
-  }
-}
-
 __device__ __forceinline__ void add192(u64& a0, u64& a1, u64& a2, long long v, int p) {
   // a += v * 2^p for a signed 64-bit v (|v| < 2^62), p <= kMaxLsb
   const bool neg = v < 0;
@@ -159,17 +137,22 @@ __device__ __forceinline__ dd to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
   return r;
 }
 
-template <int N>
+// The column sums of every thread live in shared memory (sS[j][thread], re and im),
+// so the column loop is a rolled loop over the actual n columns: the kernel body stays
+// small enough for the instruction cache.  The table row update of a step is fused
+// into the product loop.
 __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTable* __restrict__ tab) {
   extern __shared__ long long smem_cfx[];
   __shared__ dd scratch[3 * 32];
   const int n = a.n;
-  long long* sP = smem_cfx;              // +2q (re, im interleaved)
-  long long* sM = smem_cfx + 2 * n * N;  // -2q
-  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx - i * N;
-    const long long vr = (j < n) ? tab->d[2 * (i * 64 + j)] : 0;
-    const long long vi = (j < n) ? tab->d[2 * (i * 64 + j) + 1] : 0;
+  const int T = blockDim.x;
+  long long* sP = smem_cfx;            // +2q: row i, column j at 2 (i n + j) (re, im)
+  long long* sM = sP + 2 * n * n;      // -2q
+  long long* sS = sM + 2 * n * n;      // column sums: column j of thread t at 2 (j T + t)
+  for (int idx = threadIdx.x; idx < n * n; idx += T) {
+    const int i = idx / n, j = idx - i * n;
+    const long long vr = tab->d[2 * (i * 64 + j)];
+    const long long vi = tab->d[2 * (i * 64 + j) + 1];
     sP[2 * idx] = vr;
     sP[2 * idx + 1] = vi;
     sM[2 * idx] = -vr;
@@ -177,65 +160,92 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
   }
   const int e_sum = tab->e_sum;
   __syncthreads();
+  long long* mine = sS + 2 * threadIdx.x;  // column j at mine[2 j T]
 
-  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint64_t g, len;
-  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+  // aligned chunks of 2^chunk_log2 terms, 32 consecutive chunks per warp per round
+  const int lane = threadIdx.x & 31;
+  const uint64_t L = 1ull << a.chunk_log2;
+  const uint64_t c_first = a.g_begin >> a.chunk_log2;
+  const uint64_t c_end = (a.g_end + L - 1) >> a.chunk_log2;
+  const uint64_t rounds = (c_end - c_first + 31) / 32;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
 
   int e_lo = 0;
   bool anchored = false;
   u64 r0 = 0, r1 = 0, r2 = 0, i0 = 0, i1 = 0, i2 = 0;
-  long long Sr[N], Si[N];
-  for (uint64_t s = 0; s < len; ++s, ++g) {
-    if (s == 0) {
-      const uint64_t gray = g ^ (g >> 1);
-#pragma unroll
-      for (int j = 0; j < N; ++j) Sr[j] = Si[j] = 0;
-      for (int i = 0; i < n; ++i) {
-        const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + 2 * i * N;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          Sr[j] += row[2 * j];
-          Si[j] += row[2 * j + 1];
+  for (uint64_t rr = warp; rr < rounds; rr += warps) {
+    const uint64_t chunk = c_first + 32 * rr + lane;
+    uint64_t ga = chunk << a.chunk_log2, gb = ga + L;
+    if (ga < a.g_begin) ga = a.g_begin;
+    if (gb > a.g_end) gb = a.g_end;
+    if (chunk >= c_end) ga = gb = a.g_end;  // idle lane
+    for (uint64_t g = ga; g < gb; ++g) {
+      const long long* row = nullptr;  // update row of this step (null at a rebuild)
+      if (g == ga) {
+        const uint64_t gray = g ^ (g >> 1);
+        for (int j = 0; j < n; ++j) {
+          long long sr = 0, si = 0;
+          for (int i = 0; i < n; ++i) {
+            const long long* t = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + 2 * (i * n + j);
+            sr += t[0];
+            si += t[1];
+          }
+          mine[2 * j * T] = sr >> 1;
+          mine[2 * j * T + 1] = si >> 1;
+        }
+      } else {
+        const int b = ctz64(g);
+        row = (((g >> (b + 1)) & 1u) ? sP : sM) + 2 * (n - 1 - b) * n;
+      }
+      // product over the columns, (pr + i pi) 2^(E - 62), larger component in [2^61, 2^62)
+      long long pr = 0, pi = 0;
+      int E = 0;
+#pragma unroll 2
+      for (int j = 0; j < n; ++j) {
+        long long sr = mine[2 * j * T], si = mine[2 * j * T + 1];
+        if (row) {
+          sr += row[2 * j];
+          si += row[2 * j + 1];
+          mine[2 * j * T] = sr;
+          mine[2 * j * T + 1] = si;
+        }
+        const int l = norm_shift(sr, si);
+        sr <<= l;
+        si <<= l;
+        if (j == 0) {
+          pr = sr;
+          pi = si;
+          E = 62 - l;
+        } else {
+          const long long re = __mul64hi(pr, sr) - __mul64hi(pi, si);
+          const long long im = __mul64hi(pr, si) + __mul64hi(pi, sr);
+          const int l2 = norm_shift(re, im);
+          pr = re << l2;
+          pi = im << l2;
+          E += 64 - l - l2;
         }
       }
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Sr[j] = (j < n) ? (Sr[j] >> 1) : 1ll;
-        Si[j] = (j < n) ? (Si[j] >> 1) : 0ll;
+      if (pr != 0 || pi != 0) {
+        if (g & 1u) {
+          pr = -pr;
+          pi = -pi;
+        }
+        if (!anchored) {
+          e_lo = E - e_sum - kAnchorBit - 1;
+          anchored = true;
+        }
+        // a component's lsb has weight 2^(E - 62 - e_sum): bit p of the accumulators
+        int p = E - 62 - e_sum - e_lo;
+        if (p > kMaxLsb) {
+          shr192(r0, r1, r2, p - kMaxLsb);
+          shr192(i0, i1, i2, p - kMaxLsb);
+          e_lo += p - kMaxLsb;
+          p = kMaxLsb;
+        }
+        add192(r0, r1, r2, pr, p);
+        add192(i0, i1, i2, pi, p);
       }
-    } else {
-      const int b = ctz64(g);
-      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + 2 * (n - 1 - b) * N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Sr[j] += row[2 * j];
-        Si[j] += row[2 * j + 1];
-      }
-    }
-    long long pr, pi;
-    int E;
-    soft_cproduct(Sr, Si, pr, pi, E);
-    if (pr != 0 || pi != 0) {
-      if (g & 1u) {
-        pr = -pr;
-        pi = -pi;
-      }
-      if (!anchored) {
-        e_lo = E - e_sum - kAnchorBit - 1;
-        anchored = true;
-      }
-      // a component's lsb has weight 2^(E - 62 - e_sum): bit p of the accumulators
-      int p = E - 62 - e_sum - e_lo;
-      if (p > kMaxLsb) {
-        shr192(r0, r1, r2, p - kMaxLsb);
-        shr192(i0, i1, i2, p - kMaxLsb);
-        e_lo += p - kMaxLsb;
-        p = kMaxLsb;
-      }
-      add192(r0, r1, r2, pr, p);
-      add192(i0, i1, i2, pi, p);
     }
   }
 
@@ -254,53 +264,32 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
   }
 }
 
-void* pick(int n) {
-  switch ((n + 3) & ~3) {
-    case 4: return (void*)glynn_cfx_kernel<4>;
-    case 8: return (void*)glynn_cfx_kernel<8>;
-    case 12: return (void*)glynn_cfx_kernel<12>;
-    case 16: return (void*)glynn_cfx_kernel<16>;
-    case 20: return (void*)glynn_cfx_kernel<20>;
-    case 24: return (void*)glynn_cfx_kernel<24>;
-    case 28: return (void*)glynn_cfx_kernel<28>;
-    case 32: return (void*)glynn_cfx_kernel<32>;
-    case 36: return (void*)glynn_cfx_kernel<36>;
-    case 40: return (void*)glynn_cfx_kernel<40>;
-    default: return nullptr;
-  }
-}
-
-size_t smem_bytes(int n) { return 4u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long); }
+size_t smem_bytes(int n, int block) { return (4u * (size_t)n * n + 2u * (size_t)n * block) * sizeof(long long); }
 
 }  // namespace
 
-int glynn_cfx_max_n() { return 40; }
+int glynn_cfx_max_n() { return 64; }
 
 int glynn_cfx_blocks_per_sm(int n, int block) {
-  void* k = pick(n);
-  if (!k) return 0;
-  size_t smem = smem_bytes(n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem = smem_bytes(n, block);
+  cudaFuncSetAttribute((const void*)glynn_cfx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, glynn_cfx_kernel, block, smem) != cudaSuccess) return 0;
   return nb;
 }
 
 cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg& c) {
-  void* k = pick(a.n);
-  if (!k) return cudaErrorInvalidValue;
   cfx_prep_kernel<<<1, 64, 0, c.stream>>>(a, tab);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  size_t smem = smem_bytes(a.n);
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = smem_bytes(a.n, c.block);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute((const void*)glynn_cfx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   SweepArgs args = a;
   const CfxTable* tp = tab;
   void* params[] = {&args, &tp};
-  return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
+  return cudaLaunchKernel((const void*)glynn_cfx_kernel, dim3(c.grid), dim3(c.block), params, smem, c.stream);
 }
 
 }  // namespace perm

@@ -77,7 +77,9 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
 // factor is zero.  Columns are taken in pairs: the product of two column sums
 // (each below 2^62 in magnitude) is formed exactly in 128 bits, its leading 64 bits
 // are multiplied into P with the high half of a 64x64-bit product (truncation error
-// < 2^-62 per pair), and P is renormalised by at most one bit.
+// < 2^-62 per pair), and P is renormalised by at most one bit.  The value is
+// P 2^(E-63): multiplying by a pair product mc 2^(64-lz) gives h2 2^(E + 1 - lz + 63),
+// hence E += 127 - lz + top after the one-bit renormalisation.
 template <int N>
 __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, int& E, unsigned& neg) {
   static_assert(N % 2 == 0, "columns are padded to an even count");
@@ -87,26 +89,22 @@ __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, in
 #pragma unroll
   for (int j = 0; j < N; j += 2) {
     const long long qa = S[j], qb = S[j + 1];
-    neg ^= (unsigned)((u64)(qa ^ qb) >> 63);
-    const u64 aa = (qa < 0) ? (u64)(-qa) : (u64)qa;
-    const u64 ab = (qb < 0) ? (u64)(-qb) : (u64)qb;
+    const u64 sa = (u64)(qa >> 63), sb = (u64)(qb >> 63);
+    neg ^= (unsigned)(sa ^ sb);
+    // magnitudes by one's complement: |q| or |q| - 1, an error of one unit in a value
+    // of up to 2^61 (relative 2^-58 or less for all but vanishing column sums)
+    const u64 aa = (u64)qa ^ sa, ab = (u64)qb ^ sb;
     const u64 hi = __umul64hi(aa, ab), lo = aa * ab;
-    u64 mc;
-    int ec;  // the pair product is mc * 2^(ec - 64), mc normalised (or 0)
-    if (hi != 0) {
-      const int lz = __clzll((long long)hi);  // >= 4: both factors are below 2^62
-      mc = (hi << lz) | (lo >> (64 - lz));
-      ec = 128 - lz;
-    } else {
-      const int lz = __clzll((long long)lo) & 63;
-      mc = lo << lz;
-      ec = 64 - lz;
-    }
-    const u64 h2 = __umul64hi(P, mc);
+    // hi < 2^60 (both factors are below 2^62), so lz >= 4; a pair product below 2^64
+    // (vanishing column sums) keeps the bits of lo that fit, the value stays exact
+    const int lz = __clzll((long long)(hi | 1ull));
+    const u64 mc = (hi << lz) | (lo >> (64 - lz));  // pair product ~ mc * 2^(64 - lz)
+    const u64 h2 = __umul64hi(P, mc);                // P mc = h2 * 2^64 + (dropped)
     const int top = (int)(h2 >> 63);
     P = top ? h2 : (h2 << 1);
-    E += ec - 1 + top;
+    E += 127 - lz + top;
   }
+  neg &= 1u;
 }
 
 // acc += (-1)^neg * P * 2^p (p = position of P's lsb in the accumulator, p <= 127)
@@ -178,7 +176,7 @@ __device__ __forceinline__ dd acc_to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
+__global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   const bool ABS = a.want_abs != 0;
   extern __shared__ long long smem_fx[];
   __shared__ dd scratch[2 * 32];
@@ -191,7 +189,7 @@ __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
     sP[idx] = v;
     sM[idx] = -v;
   }
-  const int e_sum = tab->e_sum;
+  const int e_sum = tab->e_sum + 31 * (N - n);  // padded columns are 2^31 = 1 * 2^31
   __syncthreads();
 
   // Work: chunks of L = 2^chunk_log2 terms aligned to multiples of L; a warp takes 32
@@ -229,9 +227,10 @@ __global__ void __launch_bounds__(256, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
 #pragma unroll
           for (int j = 0; j < N; ++j) S[j] += row[j];
         }
-        // padded columns hold the constant 1 (scale 2^0, not part of e_sum)
+        // padded columns hold the constant 2^31 (their scale is counted in e_sum below),
+        // large enough that a pair of them forms a normalisable 64-bit product
 #pragma unroll
-        for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] >> 1) : 1ll;
+        for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] >> 1) : (1ll << 31);
       } else {
         const int b = ctz64(g);
         const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N;
