@@ -63,6 +63,8 @@ def _load():
                     getattr(lib, "oracle_glynn_partial%s_%s" % (c, prec)).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_glynn_partial_abs_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_ryser_partial_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_glynn_rect_grouped_%s" % prec).argtypes = [i, i, p, i64, p]
+                getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec).argtypes = [i, i, p, i64, p]
             for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
             lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
@@ -184,6 +186,30 @@ def glynn_partial_abs(A, g0: int, g1: int, prec: str = "ld") -> float:
         raise ValueError("term range outside [0, 2^(n-1)]")
     out = (ctypes.c_double * 2)()
     getattr(lib, "oracle_glynn_partial_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
+    return float(out[0]) + float(out[1])
+
+
+def glynn_rect_grouped(A, prec: str = "ld", dd: bool = False):
+    """Glynn with the rectangular padding (Eq. glynn_rectangle), the padding sign vectors
+    grouped by their number t of -1 signs (weight (-1)^t C(n-m, t)): 2^(m-1) (n-m+1)
+    products instead of 2^(n-1).  Real input."""
+    A, kind, m, n = _prepare(A)
+    if kind != "real":
+        raise TypeError("glynn_rect_grouped takes a real matrix")
+    return _call("oracle_glynn_rect_grouped", A, prec, dd)
+
+
+def glynn_rect_grouped_abs(A, prec: str = "ld") -> float:
+    """Sum of |term| over all 2^(n-1) terms of Eq. glynn_rectangle (unnormalised), evaluated
+    by the grouping of glynn_rect_grouped.  Real input."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind != "real":
+        raise TypeError("glynn_rect_grouped_abs takes a real matrix")
+    if m == 0:
+        return 1.0
+    out = (ctypes.c_double * 2)()
+    getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, out)
     return float(out[0]) + float(out[1])
 
 

@@ -21,6 +21,11 @@
  * sums are only practical for small n, the partial sums take any n); the
  * Python wrapper applies per(A) = per(A^T) for m > n and per(0 x n) = 1.
  *
+ * Functions: the definition, Glynn (square and rectangular, the appendix
+ * algorithms), Glynn with the padding rows of ones grouped by their number of -1
+ * signs (Eq. glynn_rectangle, same terms), square and rectangular Ryser, the
+ * exact subset DP, and partial sums over ranges of Glynn / Ryser terms.
+ *
  * Parity pins (tests/test_oracle_*.py): the worked 3x3 example of the usage
  * section, per(J_n) = n!, all-ones m x n = n!/(n-m)!, padded identity = 1,
  * derangement numbers, Fibonacci numbers for tridiagonal ones, triangular

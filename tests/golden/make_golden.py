@@ -54,6 +54,32 @@ def square16_f64():
     ])
 
 
+def rect20x40_f64():
+    A = inputs.rect20x40_f64()
+    t0 = time.time()
+    g = oracle.glynn_rect_grouped(A, dd=True)
+    t1 = time.time()
+    s = oracle.glynn_rect_grouped_abs(A)
+    g64 = oracle.glynn_rect_grouped(A, prec="f64")
+    # the double-precision evaluation of the same sum must agree within its own
+    # first-order rounding bound (n + 4 + 2^(m-1) (n-m+1)) u sum|t| / (2^(n-1) (n-m)!)
+    m, n = A.shape
+    norm = 2.0 ** (n - 1) * float(np.prod(np.arange(1, n - m + 1, dtype=np.float64)))
+    bound = (n + 4 + 2.0 ** (m - 1) * (n - m + 1)) * 2.0 ** -53 * s / norm
+    assert abs(g64 - (g[0] + g[1])) <= bound, (g64, g, bound)
+    write("rect20x40_f64.txt", [
+        "# 20 x 40 float64 uniform[0,1] from inputs.rect20x40_f64() (seed %d)." % (inputs.SEED_BASE + 3),
+        "# Oracle Glynn with the 20 padding rows grouped by their number of -1 signs (Eq. glynn_rectangle),",
+        "# long double (LDBL_MANT_DIG = %d), %.1f s; as double-double hi lo.  sum_abs is the sum of |term|" % (
+            oracle.ldbl_mant_dig(), t1 - t0),
+        "# over all 2^39 terms, unnormalised (the scale of any evaluation's rounding error).",
+        "seed %d" % (inputs.SEED_BASE + 3),
+        "glynn %r %r" % g,
+        "sum_abs %r" % s,
+    ])
+
+
 if __name__ == "__main__":
     square16_f64()
     square26_01()
+    rect20x40_f64()

@@ -31,6 +31,7 @@ FLOAT_ALGOS = {
     "glynn": oracle.glynn,
     "ryser": oracle.ryser,
     "ryser_rect": oracle.ryser_rect,
+    "glynn_rect_grouped": oracle.glynn_rect_grouped,
 }
 
 
@@ -164,7 +165,7 @@ def test_rank_one_closed_form(m, n):
     v = g.uniform(0.5, 1.5, n)
     A = np.outer(u, v)
     expect = math.factorial(m) * float(np.prod(u)) * _elem_sym(v, m)
-    for name in ("glynn", "ryser"):
+    for name in ("glynn", "ryser", "glynn_rect_grouped"):
         assert _rel(FLOAT_ALGOS[name](A), expect) < 1e-12, name
 
 
@@ -356,3 +357,53 @@ def test_ryser_gray_partial_sums_to_the_permanent(m, n):
     cuts = sorted(set([0, 1 << n] + [int(c) for c in g.integers(0, 1 << n, 4)]))
     parts = sum(oracle.ryser_partial(A, a, b) for a, b in zip(cuts, cuts[1:]))
     assert _rel(parts, full) < 1e-13
+
+
+# ------------------------------------------- Glynn with the padding rows grouped
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 7), (2, 6), (3, 8), (4, 10), (5, 9), (6, 6), (2, 13)])
+def test_grouped_glynn_exact_on_small_integers(m, n):
+    # integer entries in -3..3: every column sum, product and weighted sum is an integer
+    # below 2^53, so the double evaluation is exact and must equal the exact definition
+    g = inputs.rng(170 + 13 * m + n)
+    A = g.integers(-3, 4, (m, n))
+    assert oracle.glynn_rect_grouped(A.astype(np.float64), prec="f64") == float(oracle.definition(A))
+
+
+@pytest.mark.parametrize("m,n", [(1, 5), (2, 5), (3, 7), (4, 9), (5, 6), (2, 12), (6, 11), (3, 30)])
+def test_grouped_glynn_all_ones(m, n):
+    # the alternating binomial sums cancel: allow the first-order long-double bound
+    # (n + 4) eps sum|t| / (2^(n-1) (n-m)!) around the exact n! / (n-m)!
+    A = np.ones((m, n))
+    exact = math.factorial(n) // math.factorial(n - m)
+    eps = 2.0 ** -(oracle.ldbl_mant_dig() - 1)
+    bound = (n + 4) * eps * oracle.glynn_rect_grouped_abs(A) / (2.0 ** (n - 1) * math.factorial(n - m))
+    assert abs(oracle.glynn_rect_grouped(A) - exact) <= bound
+    if n <= 12:
+        assert oracle.glynn_rect_grouped(A) == exact
+
+
+@pytest.mark.parametrize("m,n", [(3, 9), (5, 11), (8, 12)])
+def test_grouped_glynn_equals_ungrouped_sum(m, n):
+    # same terms, grouped: the values agree and so do the sums of |term|
+    g = inputs.rng(180 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    assert _rel(oracle.glynn_rect_grouped(A), oracle.glynn(A)) < 1e-14
+    full_abs = oracle.glynn_partial_abs(A, 0, 1 << (n - 1))
+    assert _rel(oracle.glynn_rect_grouped_abs(A), full_abs) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(4, 7), (6, 10)])
+def test_grouped_glynn_invariants(m, n):
+    # column permutation, multilinearity in a row and scaling (the definition's invariants)
+    g = inputs.rng(190 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    p = oracle.glynn_rect_grouped(A)
+    assert _rel(oracle.glynn_rect_grouped(A[:, g.permutation(n)]), p) < 1e-13
+    B, C = A.copy(), A.copy()
+    x, y = g.uniform(-1, 1, n), g.uniform(-1, 1, n)
+    B[2], C[2] = x, y
+    S = A.copy()
+    S[2] = x + 3.0 * y
+    lhs = oracle.glynn_rect_grouped(S)
+    rhs = oracle.glynn_rect_grouped(B) + 3.0 * oracle.glynn_rect_grouped(C)
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
