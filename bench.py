@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--n", type=int, default=36, help="matrix order (36 is the benchmark workload)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "c128"],
                     help="c128: the 32x32 complex workload (profiling runs)")
-    ap.add_argument("--arith", default="auto", choices=["auto", "fp64", "fixed"])
+    ap.add_argument("--arith", default="auto", choices=["auto", "fp64", "fixed", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched 100,000-matrix leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
@@ -227,6 +227,37 @@ def run_batched(args, dev, stream):
             "launch": "one CUDA graph (size-class kernels on parallel branches)"}
 
 
+# ----------------------------------------------------------------------------- other configs
+def run_configs(dev, stream, reps=3):
+    """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
+    16x16 float64, 32x32 complex128, 20x40 float64 (grouped rectangular walk) and
+    26x26 0/1 (exact int128).  CUDA events, best of `reps` after a warm-up."""
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    cases = [("16x16 float64 uniform[-1,1]", inputs.square16_f64(), 1 << 15),
+             ("32x32 complex128 Gaussian / sqrt(2n)", inputs.square32_c128(), 1 << 31),
+             ("20x40 float64 uniform[0,1] (grouped: 2^19 x 21 terms)", inputs.rect20x40_f64(), (1 << 19) * 21),
+             ("26x26 0/1 Bernoulli(0.5), exact", inputs.square26_01(), 1 << 25)]
+    res = {}
+    for name, A, terms in cases:
+        dA = torch.from_numpy(A).to(dev)
+        out = torch.empty(2 if A.dtype.kind in "ciu" else 1, dtype=torch.float64 if A.dtype.kind != "u" else
+                          torch.int64, device=dev)
+        with torch.cuda.stream(stream):
+            capi.perm_glynn(dA, out=out, stream=stream)
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                capi.perm_glynn(dA, out=out, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        res[name] = {"ms": best, "terms_per_s": terms / (best * 1e-3)}
+    return res
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -243,7 +274,8 @@ def run_ours(args):
     A, desc = workload(args.n, args.dtype)
     n = args.n
     terms = 1 << (n - 1)
-    arith = {"auto": capi.PERM_ARITH_AUTO, "fp64": capi.PERM_ARITH_FP64, "fixed": capi.PERM_ARITH_FIXED}[args.arith]
+    arith = {"auto": capi.PERM_ARITH_AUTO, "fp64": capi.PERM_ARITH_FP64, "fixed": capi.PERM_ARITH_FIXED,
+             "mixed": capi.PERM_ARITH_MIXED}[args.arith]
     dA = torch.from_numpy(A).to(dev)
     out = torch.empty(2 if args.dtype == "c128" else 1, dtype=torch.float64, device=dev)
     err = torch.empty(1, dtype=torch.float64, device=dev)
@@ -301,12 +333,14 @@ def run_ours(args):
 
     flops_per_term = 2 * n  # n additions, n-1 multiplications, one accumulation
     achieved = flops_per_term * terms / (ms_per_step * 1e-3)
-    fixed = args.arith in ("auto", "fixed")  # auto takes the integer-pipe sweep for n >= 10
+    fixed = args.arith in ("auto", "fixed", "mixed")  # auto takes the integer-pipe sweep for n >= 10
     if fixed and n < 10:
-        fixed = args.arith == "fixed"
+        fixed = args.arith in ("fixed", "mixed")
+    mixed = fixed and args.arith in ("auto", "mixed")
     launches_per_step = 3 if fixed else 2  # [fixed-point table,] sweep, final reduction
     if fixed:
-        roof = {"bound": "alu", "pipe": "integer (ALU + IMAD); FP64 pipe idle",
+        roof = {"bound": "alu", "pipe": ("integer (ALU + IMAD) with a share of each product on the FP64 unit"
+                                         if mixed else "integer (ALU + IMAD); FP64 pipe idle"),
                 "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak_flops, "traffic": None,
                 "peak_source": "measured now: 2 x DFMA issue rate (perm_probe_rate); achieved counts the "
@@ -322,9 +356,12 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "n": n, "m": n,
-                   "arith": ("fixed: exact int64 fixed-point column sums, 64-bit-mantissa products, 192-bit "
-                             "accumulation" if fixed else "fp64: FP64 column sums re-anchored every 2^14 terms, "
-                                                          "Kahan accumulation"),
+                   "arith": (("mixed: exact int64 fixed-point column sums; products in a 64-bit-mantissa "
+                              "software float on the integer pipes, a few columns per term on the FP64 unit "
+                              "beside them; 192-bit accumulation") if mixed else
+                             ("fixed: exact int64 fixed-point column sums, 64-bit-mantissa products, 192-bit "
+                              "accumulation") if fixed else
+                             "fp64: FP64 column sums re-anchored every 2^14 terms, Kahan accumulation"),
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
         "result": result, "err_bound": err_bound,
@@ -361,6 +398,7 @@ def run_ours(args):
     if not args.no_batched:
         side = torch.cuda.Stream(dev)
         line["batched"] = run_batched(args, dev, side)
+        line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         rate, tt, wall = cpu_oracle_rate(A, args.cpu_seconds, cores)

@@ -59,11 +59,19 @@ typedef enum {
   PERM_EUNSUPPORTED = 6 /* combination of dtype / algorithm / option not provided */
 } perm_status;
 
-/* Arithmetic used by the real (PERM_F64) Glynn and Ryser sweeps. */
+/* Arithmetic of the Glynn sweeps (real and complex input; Ryser is FP64 or exact).
+ * The integer-pipe choices (FIXED, MIXED) keep exact 64-bit fixed-point column sums
+ * and sum the terms in 192-bit fixed point; for m < n they walk the real rows only,
+ * with the padding rows of ones grouped by their number of -1 signs (integer
+ * products), 2^(m-1) (n-m+1) terms instead of 2^(n-1). */
 typedef enum {
-  PERM_ARITH_AUTO = 0,  /* planner's choice: FIXED for n >= 10 unless DMMA chunk starts are asked for */
+  PERM_ARITH_AUTO = 0,  /* real: MIXED for n >= 10; complex: FIXED for n >= 10 unless an
+                           error bound is asked for; FP64 below 10 or with DMMA chunk starts */
   PERM_ARITH_FP64 = 1,  /* FP64 column sums updated by +-2 a_rj, FP64 products, Kahan sums */
-  PERM_ARITH_FIXED = 2  /* exact 64-bit fixed-point column sums, FP64 (or wider) products */
+  PERM_ARITH_FIXED = 2, /* products in a 64-bit-mantissa software float on the integer pipes */
+  PERM_ARITH_MIXED = 3  /* real Glynn: as FIXED, with the product of a few columns per term on
+                           the FP64 unit beside the integer pipes (relative error 2^-53 per
+                           such factor); other sweeps treat it as FIXED */
 } perm_arith;
 
 /* How the column sums at the start of each chunk of the Gray-code sweep are formed. */

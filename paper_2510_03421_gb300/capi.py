@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libperm.so")
 
 PERM_F64, PERM_C128, PERM_U8, PERM_I64 = 0, 1, 2, 3
 PERM_OK, PERM_EINVAL, PERM_ETOOBIG, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EUNSUPPORTED = range(7)
-PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED = 0, 1, 2
+PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED, PERM_ARITH_MIXED = 0, 1, 2, 3
 PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",

@@ -66,6 +66,8 @@ def work_log2(m, n, density, cand):
         return _log2_nodes(m, n, max(density, 1e-3))
     if cand == 1:
         return n + math.log2(max(m, 1))
+    if cand == 3 and m < n:
+        return (m - 1) + math.log2(n - m + 1) + math.log2(n)
     return (n - 1) + math.log2(max(n, 1))
 
 
@@ -112,7 +114,20 @@ def time_candidate(timer, dA, m, n, density, code, cand):
             return None
         part = timer.run(lambda: capi.perm_ryser_partial(dA, 0, TERM_SAMPLE, stream=s, opts=big))
         return part * total / TERM_SAMPLE
-    opts = dict(big, arith=2 if cand == 3 else 1)
+    if cand == 3 and m < n:
+        # the integer-pipe candidate walks a rectangle grouped: 2^(m-1) (n-m+1) terms of
+        # n columns; a long walk is timed on its first mm rows and scaled by the terms
+        opts = dict(big, arith=capi.PERM_ARITH_MIXED)
+        steps = (1 << (m - 1)) * (n - m + 1)
+        if steps <= TERM_SAMPLE * 4:
+            return timer.run(lambda: capi.perm_glynn(dA, stream=s, opts=opts))
+        mm = m
+        while mm > 1 and (1 << (mm - 1)) * (n - mm + 1) > TERM_SAMPLE:
+            mm -= 1
+        sub = dA[:mm]
+        part = timer.run(lambda: capi.perm_glynn(sub, stream=s, opts=opts))
+        return part * steps / ((1 << (mm - 1)) * (n - mm + 1))
+    opts = dict(big, arith=capi.PERM_ARITH_MIXED if cand == 3 else capi.PERM_ARITH_FP64)
     total = 1 << (n - 1)
     if total <= TERM_SAMPLE * 4:
         return timer.run(lambda: capi.perm_glynn(dA, stream=s, opts=opts))

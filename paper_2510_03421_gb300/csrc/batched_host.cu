@@ -38,20 +38,29 @@ struct Plan {
   struct Cls {
     int npad = 0;
     bool lane = false;
+    bool fx = false;  // complex warp items on the integer pipes (batched_fx.cu)
     int first_item = 0, nitems = 0;
     double cost = 0.0;
     int grid = 1;  // blocks of the class kernel (set before capture)
   };
   std::vector<Cls> classes;
   int64_t slots = 0;
+  std::vector<int32_t> fx_list;    // matrices of the integer-pipe classes
+  std::vector<int64_t> fx_offset;  // their table offsets (int64 elements), 0 for the others
+  int64_t fx_elems = 0;            // table size (int64 elements)
 };
+
+// The integer-pipe classes: complex warp items of padded order >= 16.
+inline bool fx_class(bool fixed, int dtype, bool lane, int npad) {
+  return fixed && dtype == PERM_C128 && !lane && npad >= 16 && batched_cfx_has_class(npad);
+}
 
 // Order of matrix b after the transpose rule.
 inline int order_of(int m, int n) { return m > n ? m : n; }
 inline int rows_of(int m, int n) { return m > n ? n : m; }
 
-Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, const BatchTune& t,
-                const std::vector<int32_t>* subset = nullptr) {
+Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, const BatchTune& t, bool fixed,
+                int dtype, const std::vector<int32_t>* subset = nullptr) {
   Plan p;
   const int64_t count = (int64_t)M.size();
   std::vector<std::vector<int32_t>> bucket(kClasses);
@@ -76,6 +85,7 @@ Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, co
     Plan::Cls cls;
     cls.npad = npad;
     cls.lane = lane;
+    cls.fx = fx_class(fixed, dtype, lane, npad);
     cls.first_item = (int)p.items.size();
     const int base = (int)p.order.size();
     p.order.insert(p.order.end(), v.begin(), v.end());
@@ -114,7 +124,14 @@ Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, co
       p.items.insert(p.items.end(), its.begin(), its.end());
     }
     cls.nitems = (int)p.items.size() - cls.first_item;
+    if (cls.fx) p.fx_list.insert(p.fx_list.end(), v.begin(), v.end());
     p.classes.push_back(cls);
+  }
+  p.fx_offset.assign(count, 0);
+  for (int32_t b : p.fx_list) {
+    const int n = order_of(M[b], N[b]);
+    p.fx_offset[b] = p.fx_elems;
+    p.fx_elems += 2 * (int64_t)n * n;
   }
   // largest class first: it starts the graph's branches
   std::stable_sort(p.classes.begin(), p.classes.end(),
@@ -158,7 +175,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Device layout of a plan inside bws (after the staged operand / result, if any).
 struct Layout {
-  size_t order, part_base, items, partials, done, counters, end;
+  size_t order, part_base, items, partials, done, counters, fx_list, fx_offset, fx_esum, fx_table, end;
 };
 
 Layout layout_of(const Plan& p, int64_t count, size_t start) {
@@ -169,8 +186,19 @@ Layout layout_of(const Plan& p, int64_t count, size_t start) {
   L.partials = align256(L.items + sizeof(BatchItem) * p.items.size());
   L.done = align256(L.partials + 32 * (size_t)std::max<int64_t>(p.slots, 1));
   L.counters = align256(L.done + 4 * count);
-  L.end = align256(L.counters + 4 * kClasses);
+  L.fx_list = align256(L.counters + 4 * kClasses);
+  L.fx_offset = align256(L.fx_list + 4 * p.fx_list.size());
+  L.fx_esum = align256(L.fx_offset + (p.fx_list.empty() ? 0 : 8 * count));
+  L.fx_table = align256(L.fx_esum + (p.fx_list.empty() ? 0 : 4 * count));
+  L.end = align256(L.fx_table + 8 * (size_t)p.fx_elems);
   return L;
+}
+
+// Workspace for any plan of these sizes: order, part_base, done (4 B each per matrix),
+// items and partial slots at the finest cut, and the integer-pipe tables.
+size_t plan_bound(int64_t count, size_t max_parts, size_t fx_elems_bound) {
+  return 12 * (size_t)count + 48 * (max_parts + (size_t)count) + 4 * kClasses + 16 * (size_t)count +
+         8 * fx_elems_bound + 12 * 256;
 }
 
 // Enqueue the whole batched computation of plan p on stream s (class kernels on the
@@ -179,6 +207,10 @@ int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& a
             const BatchTune& t, int64_t count, cudaStream_t s) {
   char* base = static_cast<char*>(h->bws);
   if (cudaMemsetAsync(base + L.done, 0, L.counters + 4 * kClasses - L.done, s) != cudaSuccess) return PERM_ECUDA;
+  if (!p.fx_list.empty() &&
+      launch_batched_cfx_prep(args_base, reinterpret_cast<const int32_t*>(base + L.fx_list), (int)p.fx_list.size(),
+                              s) != cudaSuccess)
+    return PERM_ECUDA;
   if (cudaEventRecord(h->fork, s) != cudaSuccess) return PERM_ECUDA;
   int k = 0;
   for (const Plan::Cls& c : p.classes) {
@@ -192,7 +224,9 @@ int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& a
     lc.block = t.block;
     lc.grid = c.grid;
     lc.stream = br;
-    if (launch_batched_class(args_base, cw, dtype, c.npad, c.lane, lc) != cudaSuccess) return PERM_ECUDA;
+    const cudaError_t e = c.fx ? launch_batched_cfx(args_base, cw, c.npad, lc)
+                               : launch_batched_class(args_base, cw, dtype, c.npad, c.lane, lc);
+    if (e != cudaSuccess) return PERM_ECUDA;
     if (cudaEventRecord(h->join[k % 16], br) != cudaSuccess) return PERM_ECUDA;
     if (cudaStreamWaitEvent(s, h->join[k % 16], 0) != cudaSuccess) return PERM_ECUDA;
     ++k;
@@ -211,8 +245,21 @@ int upload_plan(perm_handle_s* h, const Plan& p, const Layout& L, int64_t count,
   if (!p.items.empty() && cudaMemcpyAsync(base + L.items, p.items.data(), sizeof(BatchItem) * p.items.size(),
                                           cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PERM_ECUDA;
+  if (!p.fx_list.empty()) {
+    if (cudaMemcpyAsync(base + L.fx_list, p.fx_list.data(), 4 * p.fx_list.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + L.fx_offset, p.fx_offset.data(), 8 * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PERM_ECUDA;
+  }
   // the host vectors are pageable: the copies above are complete when they return
   return PERM_OK;
+}
+
+void set_fx(BatchArgs& a, perm_handle_s* h, const Layout& L) {
+  char* base = static_cast<char*>(h->bws);
+  a.fx_table = reinterpret_cast<long long*>(base + L.fx_table);
+  a.fx_offset = reinterpret_cast<const int64_t*>(base + L.fx_offset);
+  a.fx_esum = reinterpret_cast<int*>(base + L.fx_esum);
 }
 
 BatchArgs args_for(perm_handle_s* h, const Layout& L, const double* dpacked, const int64_t* doff, const int32_t* dM,
@@ -229,13 +276,14 @@ BatchArgs args_for(perm_handle_s* h, const Layout& L, const double* dpacked, con
   a.done = reinterpret_cast<int*>(base + L.done);
   a.out = dout;
   a.chunk_log2 = chunk_log2;
+  set_fx(a, h, L);
   return a;
 }
 
 // Launch-parameter tuner: time the class kernels on an evenly spaced sample of the
 // batch (at most 4096 matrices) for each candidate setting and keep the fastest.
 int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vector<int32_t>& hN, int dtype,
-               const BatchArgs& base_args, size_t start, cudaStream_t s, BatchTune* best) {
+               bool fixed, const BatchArgs& base_args, size_t start, cudaStream_t s, BatchTune* best) {
   const int64_t count = (int64_t)hM.size();
   std::vector<int32_t> sample;
   const int64_t stride = count > 4096 ? count / 4096 : 1;
@@ -254,9 +302,10 @@ int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vect
         t.n_small = ns;
         t.item_log2 = il;
         t.block = bl;
-        Plan p = build_plan(hM, hN, t, &sample);
+        Plan p = build_plan(hM, hN, t, fixed, dtype, &sample);
         for (Plan::Cls& c : p.classes) {
-          const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+          const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block)
+                               : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
           int grid = h->sms * (bps > 0 ? bps : 1);
           const int need = (c.nitems + t.block / 32 - 1) / (t.block / 32);
           c.grid = need < grid ? (need > 0 ? need : 1) : grid;
@@ -272,6 +321,7 @@ int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vect
           a.partials = reinterpret_cast<double*>(base + L.partials);
           a.done = reinterpret_cast<int*>(base + L.done);
           a.chunk_log2 = t.chunk_log2;
+          set_fx(a, h, L);
           if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;  // warm-up
           cudaEventRecord(e0, s);
           if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;
@@ -338,12 +388,14 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
   int64_t elems = 0;
   uint64_t hist = 0;
   size_t max_parts = 0;  // sub-ranges at the finest cut the tuner tries (2^14 terms)
+  size_t fx_elems = 0;   // integer-pipe tables if every matrix took them
   for (int64_t b = 0; b < count; ++b) {
     if (hM[b] < 0 || hN[b] < 0 || hoff[b] < 0) return PERM_EINVAL;
     const int n = order_of(hM[b], hN[b]);
     if (n > kMaxBatchN) return PERM_ETOOBIG;
     elems = std::max<int64_t>(elems, hoff[b] + (int64_t)hM[b] * hN[b]);
     max_parts += (n > 15) ? ((size_t)1 << (n - 15)) : 1;
+    fx_elems += 2 * (size_t)n * n;
   }
   for (int64_t b = 0; b < count; ++b) hist = mix(hist, (uint64_t)hM[b] * 131 + hN[b]);
 
@@ -371,8 +423,9 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     start = align256(start + 16 * (size_t)count);
   }
   // room for any plan: order, part_base, done (4 B each per matrix), items and partial slots
-  const size_t plan_bound = 12 * (size_t)count + 48 * (max_parts + (size_t)count) + 4 * kClasses + 8 * 256;
-  rc = ensure_bws(h, start + plan_bound);
+  // complex warp items run on the integer pipes unless FP64 arithmetic is asked for
+  const bool fixed = dtype == PERM_C128 && !(opts && opts->arith == PERM_ARITH_FP64);
+  rc = ensure_bws(h, start + plan_bound(count, max_parts, fixed ? fx_elems : 0));
   if (rc) return rc;
   char* base = static_cast<char*>(h->bws);
   const double* dpacked = static_cast<const double*>(packed);
@@ -410,7 +463,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     probe.N = dN;
     probe.out = dout;
     BatchTune best = t;
-    rc = tune_batch(h, hM, hN, dtype, probe, start, s, &best);
+    rc = tune_batch(h, hM, hN, dtype, fixed, probe, start, s, &best);
     if (rc) return rc;
     if (opts->chunk_log2) best.chunk_log2 = opts->chunk_log2;
     h->tune = best;
@@ -419,9 +472,10 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     t = best;
   }
 
-  Plan p = build_plan(hM, hN, t);
+  Plan p = build_plan(hM, hN, t, fixed, dtype);
   for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
-    const int bps = batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+    const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block)
+                         : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
     const int warps_per_block = t.block / 32;
     int grid = h->sms * (bps > 0 ? bps : 1);
     const int need = (c.nitems + warps_per_block - 1) / warps_per_block;
@@ -440,6 +494,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
   key = mix(key, (uint64_t)(uintptr_t)dN);
   key = mix(key, (uint64_t)t.n_small * 1000003ull + t.item_log2 * 1009 + t.chunk_log2 * 31 + t.block);
   key = mix(key, (uint64_t)(uintptr_t)h->bws);
+  key = mix(key, fixed ? 1u : 0u);
 
   BatchArgs args = args_for(h, L, dpacked, doff, dM, dN, dout, t.chunk_log2);
   if (!(h->cache.valid && h->cache.key == key)) {

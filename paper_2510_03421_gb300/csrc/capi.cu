@@ -96,7 +96,7 @@ int prepare(Call& c, perm_handle h, const void* A, int64_t m, int64_t n, int64_t
   c.stream = static_cast<cudaStream_t>(stream);
   c.dtype = dtype;
   c.o = opts ? *opts : perm_opts{};
-  if (c.o.arith < 0 || c.o.arith > 2 || c.o.start < 0 || c.o.start > 2 || c.o.chunk_log2 < 0 ||
+  if (c.o.arith < 0 || c.o.arith > 3 || c.o.start < 0 || c.o.start > 2 || c.o.chunk_log2 < 0 ||
       c.o.chunk_log2 > 62 || c.o.block < 0 || c.o.block > 1024 || (c.o.block % 32) != 0 || c.o.grid < 0)
     return PERM_EINVAL;
   if (m > n) {
@@ -261,38 +261,66 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
 
 // Real Glynn on the integer pipes: exact fixed-point column sums, 64-bit-mantissa
 // products, 192-bit accumulation (glynn_fx.cu).
-int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
   const bool want_abs = c.dErr != nullptr;
-  const int block = 192;  // 6 warps; two blocks per SM at up to 170 registers
+  const int block = 192;  // 6 warps; two blocks per SM at up to 168 registers
   if (c.o.block > 192) return PERM_EINVAL;
-  int bps = glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
+  // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
+  const bool grouped = !raw && c.m < c.n;
+  if (grouped) {
+    g0 = 0;
+    g1 = 1ull << (c.m - 1);
+  }
+  const int bps = grouped ? glynn_fxg_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block)
+                          : glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, mixed);
+  const uint64_t work = grouped ? (g1 - g0) * (uint64_t)(c.n - c.m + 1) : g1 - g0;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, work, 16, kRealRecord * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 12);
   if (!c.o.chunk_log2) {
-    // aligned chunks of 2^k terms, at least 32 rounds of 32 chunks per resident warp
+    // aligned chunks of 2^k steps, at least 32 rounds of 32 chunks per resident warp
     const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    const uint64_t per_step = grouped ? (uint64_t)(c.n - c.m + 1) : 1;
     int k = 12;
-    while (k > 2 && ((g1 - g0) >> k) < 1024 * warps) --k;
+    while (k > (grouped ? 0 : 2) && ((g1 - g0) >> k) * per_step < 1024 * warps) --k;
     a.chunk_log2 = k;
   }
-  if (a.chunk_log2 > 40) return PERM_ETOOBIG;  // the 192-bit accumulator holds 2^40 maximal terms per chunk
-  if (launch_glynn_fx(a, fx_table(c.h), lc, want_abs) != cudaSuccess) return PERM_ECUDA;
-  // products: n truncations of < 2^-62 each; quantisation of A: < 2^-62 of each column's
-  // absolute sum; both taken relative to sum |t|
-  const double coef = std::ldexp(2.0 * (double)c.n + 4.0, -62);
+  // the 192-bit accumulator holds 2^40 maximal terms per chunk (2^6 per grouped step)
+  if (a.chunk_log2 > (grouped ? 34 : 40)) return PERM_ETOOBIG;
+  const cudaError_t e = grouped ? launch_glynn_fxg(a, fx_table(c.h), lc, want_abs)
+                                : launch_glynn_fx(a, fx_table(c.h), lc, want_abs, mixed);
+  if (e != cudaSuccess) return PERM_ECUDA;
+  // relative error of a term against |term|: n/2 pair products of < 2^-59 each (the
+  // running mantissa keeps >= 60 bits), the quantisation of A (< 2^-62 of each
+  // column's absolute sum), the binomial weight of a grouped term (< 2^-62); the
+  // mixed variant's K columns: K conversions and K - 1 multiplications in FP64
+  const int K = (mixed && !grouped) ? glynn_fx_mixed_columns(c.n) : 0;
+  const double coef = std::ldexp((double)(c.n - K) + 5.0, -60) + std::ldexp(2.0 * K, -53);
   if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
                          static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
 }
 
+// Complex Glynn on the integer pipes: FIXED or MIXED asked for, or AUTO from n = 10;
+// not when an error bound is asked for (the complex integer-pipe sweep states none).
+bool cplx_glynn_on_integer_pipes(const Call& c) {
+  return c.n <= glynn_cfx_max_n() && !c.dErr &&
+         (c.o.arith == PERM_ARITH_FIXED || c.o.arith == PERM_ARITH_MIXED ||
+          (c.o.arith == PERM_ARITH_AUTO && c.n >= 10));
+}
+
+bool real_glynn_on_integer_pipes(const Call& c) {
+  return c.o.arith == PERM_ARITH_FIXED || c.o.arith == PERM_ARITH_MIXED ||
+         (c.o.arith == PERM_ARITH_AUTO && c.o.start != PERM_START_DMMA && c.n >= 10);
+}
+
 // Real Glynn: the integer-pipe sweep by default (faster on GB300 and at least as
-// accurate), the FP64 sweep when asked for or when the tensor-core chunk starts are.
+// accurate), mixed with the FP64 unit unless FIXED is asked for; the FP64 sweep when
+// asked for or when the tensor-core chunk starts are.
 int glynn_real(Call& c, bool raw, uint64_t g0, uint64_t g1) {
-  const bool fixed = c.o.arith == PERM_ARITH_FIXED ||
-                     (c.o.arith == PERM_ARITH_AUTO && c.o.start != PERM_START_DMMA && c.n >= 10);
-  if (fixed) return glynn_fixed(c, raw, g0, g1);
+  if (c.o.arith == PERM_ARITH_FIXED) return glynn_fixed(c, raw, g0, g1, false);
+  if (real_glynn_on_integer_pipes(c)) return glynn_fixed(c, raw, g0, g1, true);
   return glynn_fp64(c, raw, g0, g1);
 }
 
@@ -316,18 +344,26 @@ SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk)
 int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   if (c.o.block > 128) return PERM_EINVAL;
   const int block = c.n <= 40 ? 128 : 64;  // shared memory: 32 n^2 + 16 n per thread bytes
-  int bps = glynn_cfx_blocks_per_sm(c.n, c.o.block ? c.o.block : block);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kCplxRecord * sizeof(double));
+  // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
+  const bool grouped = !raw && c.m < c.n;
+  if (grouped) {
+    g0 = 0;
+    g1 = 1ull << (c.m - 1);
+  }
+  int bps = glynn_cfx_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, grouped);
+  const uint64_t per_step = grouped ? (uint64_t)(c.n - c.m + 1) : 1;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, (g1 - g0) * per_step, 16, kCplxRecord * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 12);
   if (!c.o.chunk_log2) {
     const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
     int k = 12;
-    while (k > 2 && ((g1 - g0) >> k) < 1024 * warps) --k;
+    while (k > (grouped ? 0 : 2) && ((g1 - g0) >> k) * per_step < 1024 * warps) --k;
     a.chunk_log2 = k;
   }
-  if (a.chunk_log2 > 40) return PERM_ETOOBIG;  // 2^40 maximal terms per 192-bit accumulator
-  if (launch_glynn_cfx(a, cfx_table(c.h), lc) != cudaSuccess) return PERM_ECUDA;
+  // 2^40 maximal terms per 192-bit accumulator (2^6 per grouped step)
+  if (a.chunk_log2 > (grouped ? 34 : 40)) return PERM_ETOOBIG;
+  if (launch_glynn_cfx(a, cfx_table(c.h), lc, grouped) != cudaSuccess) return PERM_ECUDA;
   if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, 0.0,
                          static_cast<double*>(c.dOut), nullptr, raw, c.stream) != cudaSuccess)
@@ -336,9 +372,7 @@ int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
 }
 
 int glynn_cplx(Call& c, bool raw, uint64_t g0, uint64_t g1) {
-  const bool fixed = c.n <= glynn_cfx_max_n() && !c.dErr &&
-                     (c.o.arith == PERM_ARITH_FIXED || (c.o.arith == PERM_ARITH_AUTO && c.n >= 10));
-  if (fixed) return glynn_cfixed(c, raw, g0, g1);
+  if (cplx_glynn_on_integer_pipes(c)) return glynn_cfixed(c, raw, g0, g1);
   if (c.n > glynn_c128_max_n()) return PERM_ETOOBIG;
   if (c.o.block > 128) return PERM_EINVAL;
   const bool want_abs = c.dErr != nullptr;
@@ -360,14 +394,21 @@ int glynn_cplx(Call& c, bool raw, uint64_t g0, uint64_t g1) {
 
 int glynn_integer(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   const int block = 256;
-  int bps = glynn_int_blocks_per_sm(c.n, c.dtype, c.o.block ? c.o.block : block);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kIntRecord * sizeof(unsigned long long));
+  // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
+  const bool grouped = !raw && c.m < c.n;
+  if (grouped) {
+    g0 = 0;
+    g1 = 1ull << (c.m - 1);
+  }
+  int bps = glynn_int_blocks_per_sm(c.n, c.dtype, c.o.block ? c.o.block : block, grouped);
+  const uint64_t work = grouped ? (g1 - g0) * (uint64_t)(c.n - c.m + 1) : g1 - g0;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, work, 16, kIntRecord * sizeof(unsigned long long));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 62);
   int* st = c.hOut ? call_status_word(c.h) : status_word(c.h);
   if (c.hOut && cudaMemsetAsync(st, 0, sizeof(int), c.stream) != cudaSuccess) return PERM_ECUDA;
   if (!raw && launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, st, c.stream) != cudaSuccess) return PERM_ECUDA;
-  if (launch_glynn_int(a, c.dtype, lc) != cudaSuccess) return PERM_ECUDA;
+  if (launch_glynn_int(a, c.dtype, lc, grouped) != cudaSuccess) return PERM_ECUDA;
   if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
                         static_cast<unsigned long long*>(c.dOut), raw, c.stream) != cudaSuccess)
@@ -569,7 +610,9 @@ void feasible(int m, int n, double density, int dtype, uint64_t cap, bool* ok) {
   ok[PERM_CAND_COMBINATORIC] = log2_perm_nodes(m, n, density) <= lcap;
   ok[PERM_CAND_RYSER] = dtype == PERM_F64 && n <= 62 && (double)n <= lcap;
   ok[PERM_CAND_GLYNN] = (double)(n - 1) <= lcap && (dtype != PERM_C128 || n <= glynn_c128_max_n());
-  ok[PERM_CAND_GLYNN_FIXED] = dtype == PERM_F64 && (double)(n - 1) <= lcap;
+  // rectangles: the grouped walk, 2^(m-1) (n-m+1) terms
+  const double lfixed = m < n ? (double)(m - 1) + std::log2((double)(n - m + 1)) : (double)(n - 1);
+  ok[PERM_CAND_GLYNN_FIXED] = dtype == PERM_F64 && lfixed <= lcap;
 }
 
 // Host-side inference of the installed model.
@@ -677,7 +720,7 @@ int run_candidate(Call& c, int cand) {
       if (c.dtype == PERM_C128) return glynn_cplx(c, false, 0, terms);
       return glynn_integer(c, false, 0, terms);
     }
-    case PERM_CAND_GLYNN_FIXED: return glynn_fixed(c, false, 0, 1ull << (c.n - 1));
+    case PERM_CAND_GLYNN_FIXED: return glynn_fixed(c, false, 0, 1ull << (c.n - 1), true);
     default: return PERM_EINVAL;
   }
 }
@@ -765,7 +808,12 @@ int perm_glynn(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
     return finish(c, out_size(dtype));
   }
   const uint64_t terms = 1ull << (c.n - 1);
-  if (terms > max_terms(c.o)) return PERM_ETOOBIG;
+  // the integer-pipe walk of a real rectangle visits 2^(m-1) (n-m+1) grouped terms
+  const bool grouped = c.m < c.n && ((dtype == PERM_F64 && real_glynn_on_integer_pipes(c)) ||
+                                     (dtype == PERM_C128 && cplx_glynn_on_integer_pipes(c)) ||
+                                     dtype == PERM_U8 || dtype == PERM_I64);
+  const uint64_t visited = grouped ? (1ull << (c.m - 1)) * (uint64_t)(c.n - c.m + 1) : terms;
+  if (visited > max_terms(c.o)) return PERM_ETOOBIG;
   switch (dtype) {
     case PERM_F64: rc = glynn_real(c, false, 0, terms); break;
     case PERM_C128: rc = glynn_cplx(c, false, 0, terms); break;

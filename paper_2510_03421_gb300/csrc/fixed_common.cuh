@@ -1,6 +1,7 @@
-// Fixed-point helpers shared by the complex integer-pipe sweeps (glynn_cfx.cu,
-// batched_fx.cu): normalisation of a complex software float whose two signed 64-bit
-// components share one exponent, and signed 192-bit fixed-point accumulators.
+// Fixed-point helpers shared by the integer-pipe sweeps (glynn_fx.cu, glynn_fxg.cu,
+// glynn_cfx.cu): the real software-float product of column sums, the normalisation of
+// a complex software float whose two signed 64-bit components share one exponent,
+// and signed 192-bit fixed-point accumulators.
 #pragma once
 
 #include "device_common.cuh"
@@ -8,6 +9,125 @@
 namespace perm {
 
 typedef unsigned long long u64;
+
+constexpr int kAnchorBit = 120;  // leading bit of a thread's first term in its accumulator
+constexpr int kMaxLsb = 87;      // a term's lsb may sit at most here (leading bit <= 150)
+
+// Full 64 x 64 -> 128-bit unsigned product as one carry chain of 32-bit multiply-adds.
+__device__ __forceinline__ void mul_wide(u64 a, u64 b, u64& lo, u64& hi) {
+  asm("{\n\t.reg .u32 a0, a1, b0, b1, r0, r1, r2, r3;\n\t"
+      "mov.b64 {a0, a1}, %2;\n\t"
+      "mov.b64 {b0, b1}, %3;\n\t"
+      "mul.lo.u32 r0, a0, b0;\n\t"
+      "mul.hi.u32 r1, a0, b0;\n\t"
+      "mad.lo.cc.u32 r1, a0, b1, r1;\n\t"
+      "madc.hi.u32 r2, a0, b1, 0;\n\t"
+      "mad.lo.cc.u32 r1, a1, b0, r1;\n\t"
+      "madc.hi.cc.u32 r2, a1, b0, r2;\n\t"
+      "madc.hi.u32 r3, a1, b1, 0;\n\t"
+      "mad.lo.cc.u32 r2, a1, b1, r2;\n\t"
+      "addc.u32 r3, r3, 0;\n\t"
+      "mov.b64 %0, {r0, r1};\n\t"
+      "mov.b64 %1, {r2, r3};\n\t}"
+      : "=l"(lo), "=l"(hi)
+      : "l"(a), "l"(b));
+}
+
+// value = sign * P * 2^(E - 63) * 2^(-e_sum); P == 0 iff some factor is zero.
+// Columns [0, N - K) are taken in pairs: the product of two column sums (each at
+// most 2^61 in magnitude) is formed exactly in 128 bits and its leading 64 bits mc
+// (normalised, value mc 2^(64 - lz)) are multiplied into P with the high half of a
+// 64x64-bit product: P mc 2^(E - 63 + 64 - lz) = h2 2^(E + 65 - lz), so P = h2 and
+// E += 128 - lz.  h2 >= P / 2, so P is renormalised (clz) only every fourth pair and
+// after the last one.  Columns [N - K, N) are multiplied on the FP64 unit and the
+// double product is folded in once (its exponent field ed: value md 2^(ed - 1086)).
+template <int N, int K>
+__device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, int& E, unsigned& neg) {
+  static_assert((N - K) % 2 == 0, "integer columns are taken in pairs");
+  P = 1ull << 63;  // the value 1
+  E = 0;
+  neg = 0;
+#pragma unroll
+  for (int j = 0; j < N - K; j += 2) {
+    const long long qa = S[j], qb = S[j + 1];
+    const u64 sa = (u64)(qa >> 63), sb = (u64)(qb >> 63);
+    neg ^= (unsigned)(sa ^ sb);
+    // magnitudes by one's complement: |q| or |q| - 1, an error of one unit in a value
+    // of up to 2^61 (relative 2^-58 or less for all but vanishing column sums)
+    const u64 aa = (u64)qa ^ sa, ab = (u64)qb ^ sb;
+    u64 lo, hi;
+    mul_wide(aa, ab, lo, hi);
+    // hi < 2^59, so lz >= 5; a pair product below 2^64 (vanishing column sums) keeps
+    // the bits of lo that fit, the value stays exact
+    const int lz = __clzll((long long)(hi | 1ull));
+    const u64 mc = (hi << lz) | (lo >> (64 - lz));
+    P = __umul64hi(P, mc);
+    E += 128 - lz;
+    if ((j / 2) % 4 == 3 || j + 2 >= N - K) {
+      const int l = __clzll((long long)(P | 1ull));  // P == 0 stays 0
+      P <<= l;
+      E -= l;
+    }
+  }
+  if (K > 0) {
+    double d[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = (double)S[N - K + k];  // exact below 2^53, else rounded once
+#pragma unroll
+    for (int w = 1; w < K; w *= 2)
+#pragma unroll
+      for (int k = 0; k + w < K; k += 2 * w) d[k] = __dmul_rn(d[k], d[k + w]);
+    // |d| < 2^(61 K) <= 2^976 (K <= 16) and |d| >= 1 unless some factor is 0: no overflow,
+    // no subnormals, and ed == 0 exactly when the product is zero
+    const u64 bits = (u64)__double_as_longlong(d[0]);
+    neg ^= (unsigned)(bits >> 63);
+    const int ed = (int)((bits >> 52) & 0x7ff);
+    const u64 md = (bits << 11) | (1ull << 63);
+    const u64 h2 = __umul64hi(P, md);
+    const int top = (int)(h2 >> 63);
+    P = ed ? (top ? h2 : (h2 << 1)) : 0ull;
+    E += ed - 1023 + top;
+  }
+  neg &= 1u;
+}
+
+// acc += (-1)^neg * P * 2^p (p = position of P's lsb in the accumulator, p <= 127)
+__device__ __forceinline__ void acc_add(u64& a0, u64& a1, u64& a2, u64 P, int p, unsigned neg) {
+  u64 t0, t1, t2;
+  if (p >= 64) {
+    const int q = p - 64;
+    t0 = 0;
+    t1 = P << q;
+    t2 = q ? (P >> (64 - q)) : 0;
+  } else if (p >= 0) {
+    t0 = P << p;
+    t1 = p ? (P >> (64 - p)) : 0;
+    t2 = 0;
+  } else if (p > -64) {
+    t0 = P >> (-p);
+    t1 = 0;
+    t2 = 0;
+  } else {
+    t0 = t1 = t2 = 0;
+  }
+  if (neg) {
+    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+        : "+l"(a0), "+l"(a1), "+l"(a2)
+        : "l"(t0), "l"(t1), "l"(t2));
+  } else {
+    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+        : "+l"(a0), "+l"(a1), "+l"(a2)
+        : "l"(t0), "l"(t1), "l"(t2));
+  }
+}
+
+// u64 binomial coefficient C(a, b), a <= 63 (exact: every partial product is a
+// binomial coefficient times b, below 2^70, kept in 128 bits).
+__device__ __forceinline__ u64 binom_u64(int a, int b) {
+  unsigned __int128 r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (unsigned __int128)(a - b + i) / (unsigned __int128)i;
+  return (u64)r;
+}
 
 __device__ __forceinline__ u64 uabs(long long v) { return v < 0 ? (u64)(-v) : (u64)v; }
 

@@ -8,9 +8,15 @@
 //     (relative perturbation <= 2^-62 of the column's absolute sum, far below the
 //     rounding of the input to double).  The +-2 q updates of the Gray-code walk are
 //     exact int64 additions, so the column sums never drift and need no re-anchoring;
-//   * the product over columns is a software float with a 64-bit mantissa: each
-//     factor is normalised with clz and multiplied with the high half of a 64x64-bit
-//     product (truncation error < 2^-62 per factor, below FP64's 2^-53);
+//   * the product over columns is a software float with a 64-bit mantissa: column
+//     sums are multiplied in pairs (exact 128-bit product, normalised with clz) into
+//     the running mantissa with the high half of a 64x64-bit product; the running
+//     mantissa is renormalised every fourth pair, so it keeps at least 60 bits
+//     (truncation error < 2^-59 per pair, against FP64's 2^-53 per multiplication);
+//   * "mixed" variants (template K > 0) take the product of the last K columns on
+//     the otherwise idle FP64 unit (int64 -> double conversions and K - 1 DMUL,
+//     2^-53 each) and fold it into the mantissa once: the FP64 pipe and the integer
+//     pipes run side by side;
 //   * the signed terms are added into a 192-bit fixed-point accumulator per thread.
 //     Its window is anchored on the thread's first nonzero term (whose leading bit
 //     lands on bit 120, leaving 120 bits below it and 70 above); a later term whose
@@ -18,15 +24,11 @@
 //     is converted to double-double once and reduced as in the FP64 path.
 // The preparation kernel derives the scales and the quantised tables on the device.
 #include "device_common.cuh"
+#include "fixed_common.cuh"
 #include "internal.h"
 
 namespace perm {
 namespace {
-
-typedef unsigned long long u64;
-
-constexpr int kAnchorBit = 120;  // leading bit of a thread's first term
-constexpr int kMaxLsb = 87;      // a term's lsb may sit at most here (leading bit <= 150)
 
 // One block, one thread per column: scales, quantised +-2q tables and exponents.
 __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
@@ -73,111 +75,8 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
   }
 }
 
-// value = sign * P * 2^(E - 63) * 2^(-e_sum), P in [2^63, 2^64); P == 0 iff some
-// factor is zero.  Columns are taken in pairs: the product of two column sums
-// (each below 2^62 in magnitude) is formed exactly in 128 bits, its leading 64 bits
-// are multiplied into P with the high half of a 64x64-bit product (truncation error
-// < 2^-62 per pair), and P is renormalised by at most one bit.  The value is
-// P 2^(E-63): multiplying by a pair product mc 2^(64-lz) gives h2 2^(E + 1 - lz + 63),
-// hence E += 127 - lz + top after the one-bit renormalisation.
-template <int N>
-__device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, int& E, unsigned& neg) {
-  static_assert(N % 2 == 0, "columns are padded to an even count");
-  P = 1ull << 63;  // the value 1
-  E = 0;
-  neg = 0;
-#pragma unroll
-  for (int j = 0; j < N; j += 2) {
-    const long long qa = S[j], qb = S[j + 1];
-    const u64 sa = (u64)(qa >> 63), sb = (u64)(qb >> 63);
-    neg ^= (unsigned)(sa ^ sb);
-    // magnitudes by one's complement: |q| or |q| - 1, an error of one unit in a value
-    // of up to 2^61 (relative 2^-58 or less for all but vanishing column sums)
-    const u64 aa = (u64)qa ^ sa, ab = (u64)qb ^ sb;
-    const u64 hi = __umul64hi(aa, ab), lo = aa * ab;
-    // hi < 2^60 (both factors are below 2^62), so lz >= 4; a pair product below 2^64
-    // (vanishing column sums) keeps the bits of lo that fit, the value stays exact
-    const int lz = __clzll((long long)(hi | 1ull));
-    const u64 mc = (hi << lz) | (lo >> (64 - lz));  // pair product ~ mc * 2^(64 - lz)
-    const u64 h2 = __umul64hi(P, mc);                // P mc = h2 * 2^64 + (dropped)
-    const int top = (int)(h2 >> 63);
-    P = top ? h2 : (h2 << 1);
-    E += 127 - lz + top;
-  }
-  neg &= 1u;
-}
-
-// acc += (-1)^neg * P * 2^p (p = position of P's lsb in the accumulator, p <= 127)
-__device__ __forceinline__ void acc_add(u64& a0, u64& a1, u64& a2, u64 P, int p, unsigned neg) {
-  u64 t0, t1, t2;
-  if (p >= 64) {
-    const int q = p - 64;
-    t0 = 0;
-    t1 = P << q;
-    t2 = q ? (P >> (64 - q)) : 0;
-  } else if (p >= 0) {
-    t0 = P << p;
-    t1 = p ? (P >> (64 - p)) : 0;
-    t2 = 0;
-  } else if (p > -64) {
-    t0 = P >> (-p);
-    t1 = 0;
-    t2 = 0;
-  } else {
-    t0 = t1 = t2 = 0;
-  }
-  if (neg) {
-    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
-        : "+l"(a0), "+l"(a1), "+l"(a2)
-        : "l"(t0), "l"(t1), "l"(t2));
-  } else {
-    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
-        : "+l"(a0), "+l"(a1), "+l"(a2)
-        : "l"(t0), "l"(t1), "l"(t2));
-  }
-}
-
-// Arithmetic right shift of the signed 192-bit integer a2:a1:a0 by s >= 1 bits.
-__device__ __forceinline__ void shr192(u64& a0, u64& a1, u64& a2, int s) {
-  const u64 sgn = (u64)((long long)a2 >> 63);
-  while (s >= 64) {
-    a0 = a1;
-    a1 = a2;
-    a2 = sgn;
-    s -= 64;
-  }
-  if (s > 0) {
-    a0 = (a0 >> s) | (a1 << (64 - s));
-    a1 = (a1 >> s) | (a2 << (64 - s));
-    a2 = (u64)((long long)a2 >> s);
-  }
-}
-
-// Signed 192-bit integer times 2^e_lo as a double-double (four exact 48-bit pieces).
-__device__ __forceinline__ dd acc_to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
-  const bool negative = (long long)a2 < 0;
-  if (negative) {
-    asm("sub.cc.u64 %0, 0, %0;\n\tsubc.cc.u64 %1, 0, %1;\n\tsubc.u64 %2, 0, %2;" : "+l"(a0), "+l"(a1), "+l"(a2));
-  }
-  const u64 mask = (1ull << 48) - 1;
-  const double p0 = (double)(a0 & mask);
-  const double p1 = (double)(((a0 >> 48) | (a1 << 16)) & mask);
-  const double p2 = (double)(((a1 >> 32) | (a2 << 32)) & mask);
-  const double p3 = (double)(a2 >> 16);
-  dd r = dd{scalbn(p3, e_lo + 144), 0.0};
-  r = dd_add(r, dd{scalbn(p2, e_lo + 96), 0.0});
-  r = dd_add(r, dd{scalbn(p1, e_lo + 48), 0.0});
-  r = dd_add(r, dd{scalbn(p0, e_lo), 0.0});
-  if (negative) {
-    r.hi = -r.hi;
-    r.lo = -r.lo;
-  }
-  return r;
-}
-
-template <int N>
+template <int N, int K, bool ABS>
 __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
-  const bool ABS = a.want_abs != 0;
   extern __shared__ long long smem_fx[];
   __shared__ dd scratch[2 * 32];
   const int n = a.n;
@@ -240,7 +139,7 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
       u64 P;
       int E;
       unsigned neg;
-      soft_product(S, P, E, neg);
+      soft_product<N, K>(S, P, E, neg);
       if (P != 0) {
         if (!anchored) {
           e_lo = E - e_sum - kAnchorBit;
@@ -259,7 +158,7 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
     }
   }
 
-  dd v[2] = {acc_to_dd(a0, a1, a2, e_lo), ABS ? acc_to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0}};
+  dd v[2] = {to_dd(a0, a1, a2, e_lo), ABS ? to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0}};
   block_sum_dd<2>(v, scratch);
   if (threadIdx.x == 0) {
     double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
@@ -271,29 +170,39 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepA
   }
 }
 
+// Columns multiplied on the FP64 unit by the mixed variant, per padded order: enough
+// to move a share of the work off the integer pipes, few enough that the FP64 unit
+// (2K - 1 operations per term at 1/74 of the integer rate) is not the bottleneck.
+// Measured on GB300 (terms/s, K = 0 -> best K): N = 28: 2.73e10 -> 2.95e10 (K = 4);
+// N = 32: 2.54e10 -> 2.82e10 (K = 6); N = 36: 2.31e10 -> 2.60e10 (K = 8).  From N = 40
+// one block of 6 warps per SM is resident and the FP64 latency is no longer hidden.
+constexpr int mixed_columns(int N) { return N >= 40 ? 0 : N >= 36 ? 8 : N >= 32 ? 6 : N >= 16 ? 4 : 0; }
+
 template <int N>
-void* kernel_for(bool) {
-  return (void*)glynn_fx_kernel<N>;
+void* kernel_for(bool mixed, bool abs) {
+  constexpr int K = mixed_columns(N);
+  if (mixed && K > 0) return abs ? (void*)glynn_fx_kernel<N, K, true> : (void*)glynn_fx_kernel<N, K, false>;
+  return abs ? (void*)glynn_fx_kernel<N, 0, true> : (void*)glynn_fx_kernel<N, 0, false>;
 }
 
-void* pick(int n, bool abs) {
+void* pick(int n, bool mixed, bool abs) {
   switch ((n + 3) & ~3) {
-    case 4: return kernel_for<4>(abs);
-    case 8: return kernel_for<8>(abs);
-    case 12: return kernel_for<12>(abs);
-    case 16: return kernel_for<16>(abs);
-    case 20: return kernel_for<20>(abs);
-    case 24: return kernel_for<24>(abs);
-    case 28: return kernel_for<28>(abs);
-    case 32: return kernel_for<32>(abs);
-    case 36: return kernel_for<36>(abs);
-    case 40: return kernel_for<40>(abs);
-    case 44: return kernel_for<44>(abs);
-    case 48: return kernel_for<48>(abs);
-    case 52: return kernel_for<52>(abs);
-    case 56: return kernel_for<56>(abs);
-    case 60: return kernel_for<60>(abs);
-    case 64: return kernel_for<64>(abs);
+    case 4: return kernel_for<4>(mixed, abs);
+    case 8: return kernel_for<8>(mixed, abs);
+    case 12: return kernel_for<12>(mixed, abs);
+    case 16: return kernel_for<16>(mixed, abs);
+    case 20: return kernel_for<20>(mixed, abs);
+    case 24: return kernel_for<24>(mixed, abs);
+    case 28: return kernel_for<28>(mixed, abs);
+    case 32: return kernel_for<32>(mixed, abs);
+    case 36: return kernel_for<36>(mixed, abs);
+    case 40: return kernel_for<40>(mixed, abs);
+    case 44: return kernel_for<44>(mixed, abs);
+    case 48: return kernel_for<48>(mixed, abs);
+    case 52: return kernel_for<52>(mixed, abs);
+    case 56: return kernel_for<56>(mixed, abs);
+    case 60: return kernel_for<60>(mixed, abs);
+    case 64: return kernel_for<64>(mixed, abs);
     default: return nullptr;
   }
 }
@@ -302,29 +211,37 @@ size_t smem_bytes(int n) { return 2u * (size_t)n * (size_t)((n + 3) & ~3) * size
 
 }  // namespace
 
-int glynn_fx_blocks_per_sm(int n, int block, bool want_abs) {
-  void* k = pick(n, want_abs);
+int glynn_fx_mixed_columns(int n) {
+  const int N = (n + 3) & ~3;
+  return N >= 40 ? 0 : mixed_columns(N);
+}
+
+int glynn_fx_blocks_per_sm(int n, int block, bool mixed) {
+  void* k = pick(n, mixed, false);
   if (!k) return 0;
-  size_t smem = smem_bytes(n);
+  const size_t smem = smem_bytes(n);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
 }
 
-cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs) {
-  void* k = pick(a.n, want_abs);
+cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream) {
+  fx_prep_kernel<<<1, 64, 0, stream>>>(a, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed) {
+  void* k = pick(a.n, mixed, want_abs);
   if (!k) return cudaErrorInvalidValue;
-  fx_prep_kernel<<<1, 64, 0, c.stream>>>(a, tab);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_fx_prep(a, tab, c.stream);
   if (e != cudaSuccess) return e;
-  size_t smem = smem_bytes(a.n);
+  const size_t smem = smem_bytes(a.n);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   SweepArgs args = a;
-  args.want_abs = want_abs ? 1 : 0;
   const FxTable* tp = tab;
   void* params[] = {&args, &tp};
   return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);

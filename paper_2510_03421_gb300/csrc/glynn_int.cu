@@ -92,6 +92,124 @@ __global__ void __launch_bounds__(256) glynn_int_kernel(SweepArgs a) {
   }
 }
 
+// Rectangular Glynn (Eq. glynn_rectangle) with the n - m padding rows of ones grouped
+// by their number t of -1 signs: column sums shifted by n - m - 2t, sign (-1)^t,
+// multiplicity C(n - m, t) (an exact integer weight).  The walk runs over the
+// 2^(m-1) sign vectors of the real rows (bit b of gray(g) <-> row m-1-b, term sign
+// (-1)^g); at each it takes the n - m + 1 values of t, up for even g and down for odd
+// g, one padding update (+-2 per column) apart.  Products, weights and the signed sum
+// are exact modulo 2^128, so the total is the same sum as the ungrouped walk's.
+template <int N, typename T>
+__global__ void __launch_bounds__(256) glynn_intg_kernel(SweepArgs a) {
+  extern __shared__ long long smem_i[];
+  __shared__ u128 scratch[32];
+  __shared__ unsigned long long s_w[64];  // C(n - m, t)
+  const int n = a.n, m = a.m, k = n - m;
+  const int R = m + 1;                    // the real rows and one padding row
+  long long* sP = smem_i;                 // +2 a'_ij
+  long long* sM = smem_i + R * N;         // -2 a'_ij
+  for (int idx = threadIdx.x; idx < R * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    long long v = 0;
+    if (j < n) v = (i < m) ? load_int<T>(a.A, i * a.rs + j * a.cs) : 1;
+    sP[idx] = 2 * v;
+    sM[idx] = -2 * v;
+  }
+  for (int t = threadIdx.x; t <= k; t += blockDim.x) {
+    u128 c = 1;
+    for (int i = 1; i <= t; ++i) c = c * (u128)(k - t + i) / (u128)i;
+    s_w[t] = (unsigned long long)c;
+  }
+  __syncthreads();
+  const long long* padP = sP + m * N;
+  const long long* padM = sM + m * N;
+
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t g, len;
+  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+
+  u128 acc = 0;
+  long long S[N];
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    const bool up = (g & 1u) == 0;
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = 0;
+      for (int i = 0; i < m; ++i) {
+        const long long* row = (((gray >> (m - 1 - i)) & 1u) ? sM : sP) + i * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[j] += row[j];
+      }
+      const long long* pad = up ? padP : padM;  // padding sum +k (t = 0) or -k (t = k)
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] + (long long)k * pad[j]) / 2 : 1;
+    } else {
+      const int b = ctz64(g);
+      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (m - 1 - b) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] += row[j];
+    }
+    for (int st = 0; st <= k; ++st) {
+      if (st > 0) {
+        const long long* pad = up ? padM : padP;
+#pragma unroll
+        for (int j = 0; j < N; ++j) S[j] += pad[j];
+      }
+      const int t = up ? st : k - st;
+      u128 P = (u128)(__int128)S[0];
+#pragma unroll
+      for (int j = 1; j < N; ++j) P = mul_s64(P, S[j]);
+      P *= (u128)s_w[t];
+      if (((unsigned)(g & 1u) ^ (unsigned)(t & 1)) != 0u) acc -= P; else acc += P;
+    }
+  }
+
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += shfl_down_u128(acc, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) scratch[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    u128 x = (lane < nw) ? scratch[lane] : (u128)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += shfl_down_u128(x, off);
+    if (lane == 0) {
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials) + (size_t)blockIdx.x * kIntRecord;
+      rec[0] = (unsigned long long)x;
+      rec[1] = (unsigned long long)(x >> 64);
+    }
+  }
+}
+
+template <int N>
+void* kernel_for_grouped(int dtype) {
+  return dtype == 2 ? (void*)glynn_intg_kernel<N, unsigned char> : (void*)glynn_intg_kernel<N, long long>;
+}
+
+void* pick_grouped(int n, int dtype) {
+  switch ((n + 3) & ~3) {
+    case 4: return kernel_for_grouped<4>(dtype);
+    case 8: return kernel_for_grouped<8>(dtype);
+    case 12: return kernel_for_grouped<12>(dtype);
+    case 16: return kernel_for_grouped<16>(dtype);
+    case 20: return kernel_for_grouped<20>(dtype);
+    case 24: return kernel_for_grouped<24>(dtype);
+    case 28: return kernel_for_grouped<28>(dtype);
+    case 32: return kernel_for_grouped<32>(dtype);
+    case 36: return kernel_for_grouped<36>(dtype);
+    case 40: return kernel_for_grouped<40>(dtype);
+    case 44: return kernel_for_grouped<44>(dtype);
+    case 48: return kernel_for_grouped<48>(dtype);
+    case 52: return kernel_for_grouped<52>(dtype);
+    case 56: return kernel_for_grouped<56>(dtype);
+    case 60: return kernel_for_grouped<60>(dtype);
+    case 64: return kernel_for_grouped<64>(dtype);
+    default: return nullptr;
+  }
+}
+
 template <int N>
 void* kernel_for(int dtype) {
   return dtype == 2 ? (void*)glynn_int_kernel<N, unsigned char> : (void*)glynn_int_kernel<N, long long>;
@@ -170,20 +288,21 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
 
 }  // namespace
 
-int glynn_int_blocks_per_sm(int n, int dtype, int block) {
-  void* k = pick(n, dtype);
+int glynn_int_blocks_per_sm(int n, int dtype, int block, bool grouped) {
+  void* k = grouped ? pick_grouped(n, dtype) : pick(n, dtype);
   if (!k) return 0;
-  size_t smem = smem_bytes(n);
+  size_t smem = smem_bytes(n);  // at least the grouped walk's (m + 1) rows
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
 }
 
-cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c) {
-  void* k = pick(a.n, dtype);
+cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c, bool grouped) {
+  if (grouped && (a.m < 1 || a.m >= a.n)) return cudaErrorInvalidValue;
+  void* k = grouped ? pick_grouped(a.n, dtype) : pick(a.n, dtype);
   if (!k) return cudaErrorInvalidValue;
-  size_t smem = smem_bytes(a.n);
+  size_t smem = grouped ? 2u * (size_t)(a.m + 1) * (size_t)((a.n + 3) & ~3) * sizeof(long long) : smem_bytes(a.n);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

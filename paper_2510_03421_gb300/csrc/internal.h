@@ -51,8 +51,15 @@ struct FxTable {
   int bad;    // a non-finite entry was seen
   int pad;
 };
-cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
-int glynn_fx_blocks_per_sm(int n, int block, bool want_abs);
+// mixed: the last glynn_fx_mixed_columns(n) columns' product runs on the FP64 unit
+cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream);
+cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed);
+int glynn_fx_blocks_per_sm(int n, int block, bool mixed);
+int glynn_fx_mixed_columns(int n);
+// grouped rectangular walk (1 <= m < n; glynn_fxg.cu): g ranges over [0, 2^(m-1)),
+// n - m + 1 terms each
+cudaError_t launch_glynn_fxg(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
+int glynn_fxg_blocks_per_sm(int m, int n, int block);
 
 // --- Glynn, complex input on the integer pipes (glynn_cfx.cu); n <= glynn_cfx_max_n()
 struct CfxTable {
@@ -60,8 +67,9 @@ struct CfxTable {
   int e_sum;
   int bad;
 };
-cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg& c);
-int glynn_cfx_blocks_per_sm(int n, int block);
+// grouped: the rectangular walk over the 2^(m-1) real-row sign vectors (1 <= m < n)
+cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg& c, bool grouped);
+int glynn_cfx_blocks_per_sm(int m, int n, int block, bool grouped);
 int glynn_cfx_max_n();
 
 // --- Glynn, complex FP64 (glynn_c128.cu); n <= glynn_c128_max_n()
@@ -70,8 +78,9 @@ int glynn_c128_blocks_per_sm(int n, int block, bool want_abs);
 int glynn_c128_max_n();
 
 // --- Glynn, exact integer (glynn_int.cu); dtype 2 = uint8, 3 = int64
-cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c);
-int glynn_int_blocks_per_sm(int n, int dtype, int block);
+// grouped: the rectangular walk over the 2^(m-1) real-row sign vectors (1 <= m < n)
+cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c, bool grouped);
+int glynn_int_blocks_per_sm(int n, int dtype, int block, bool grouped);
 // a-priori int128 range check; writes 3 (PERM_EOVERFLOW) to *status if exactness is not assured
 cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
                              cudaStream_t s);
@@ -128,10 +137,21 @@ struct BatchArgs {
   int* done;                // sub-ranges finished per matrix (zeroed before the launch)
   double* out;              // results (complex: (re, im) pairs)
   int chunk_log2;
+  // integer-pipe classes (batched_fx.cu): quantised +2q tables, n rows of 2n int64 per
+  // matrix at fx_table + fx_offset[b], and the sum of the column exponents
+  long long* fx_table;
+  const int64_t* fx_offset;
+  int* fx_esum;
 };
+constexpr int kFxBad = -2147483647 - 1;  // fx_esum of a matrix with a non-finite entry
 cudaError_t launch_batched_class(const BatchArgs& a, const ClassWork& c, int dtype, int npad, bool lane,
                                  const LaunchCfg& lc);
 int batched_blocks_per_sm(int dtype, int npad, bool lane, int block);
+// complex warp-item classes on the integer pipes (batched_fx.cu)
+bool batched_cfx_has_class(int npad);
+int batched_cfx_blocks_per_sm(int npad, int block);
+cudaError_t launch_batched_cfx_prep(const BatchArgs& a, const int32_t* list, int count, cudaStream_t stream);
+cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc);
 }  // namespace perm
 struct perm_handle_s;
 namespace perm {

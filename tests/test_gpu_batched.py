@@ -76,16 +76,45 @@ def test_haar_blocks_split_items_and_host_buffers(capi, dev):
     out = capi.perm_batched(tp, to, tM, tN, opts=dict(chunk_log2=10))
     torch.cuda.synchronize(dev)
     got = results(capi, out, capi.PERM_C128, len(sizes))
+    big = [b for b in range(len(sizes)) if sizes[b] > 13][::6]  # a sample of the split matrices
     for b, n in enumerate(sizes):
         A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
-        single = capi.value(capi.perm_glynn(torch.from_numpy(A).to(dev)), capi.PERM_C128)
-        close(got[b], single, A)
         if n <= 13:
             close(got[b], oracle.glynn(A), A)
-    host_out = capi.perm_batched(packed, offsets, M, N)  # numpy in, numpy out
+        elif b in big:
+            close(got[b], oracle.glynn(A, prec="f64"), A)
+    host_out = capi.perm_batched(packed, offsets, M, N)  # numpy in, numpy out: the same computation
     for b in range(len(sizes)):
-        n = int(sizes[b])
-        close(capi.value(host_out, capi.PERM_C128, b), got[b], packed[offsets[b]: offsets[b] + n * n].reshape(n, n))
+        assert capi.value(host_out, capi.PERM_C128, b) == got[b]
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
+    # padded orders 16..32 (n = 13..32) are warp items; by default they run on the integer
+    # pipes (batched_fx.cu), with opts.arith = FP64 on the FP64 class kernels.  Square,
+    # rectangular and transposed shapes, a matrix with a non-finite entry, an empty one.
+    import torch
+    g = inputs.rng(9650 + arith)
+    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (21, 23), (6, 26), (22, 22), (0, 18),
+              (12, 18)]
+    mats = [(g.standard_normal(s) + 1j * g.standard_normal(s)) / np.sqrt(2 * max(s)) for s in shapes]
+    mats[-1][3, 4] = np.nan
+    packed, offsets, M, N = pack(mats, np.complex128)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN, opts=dict(arith=arith))
+    torch.cuda.synchronize(dev)
+    got = results(capi, out, capi.PERM_C128, len(mats))
+    for A, x in zip(mats[:-1], got[:-1]):
+        m, n = sorted(A.shape)
+        if m == 0:
+            assert x == 1
+        elif n <= 16:
+            close(x, oracle.glynn(A), A)
+        elif m < n and n >= 21:
+            close(x, oracle.ryser_rect(A if A.shape[0] <= A.shape[1] else A.T, prec="f64"), A)
+        else:
+            close(x, oracle.glynn(A, prec="f64"), A)
+    assert np.isnan(got[-1].real) and np.isnan(got[-1].imag)
 
 
 def test_graph_replay_sees_new_data(capi, dev):
@@ -117,13 +146,13 @@ def test_tuner_keeps_results(capi, dev):
     sizes, packed, offsets = inputs.batched_haar(400, 4, 16, 9801)
     M = sizes.astype(np.int32)
     tp, to, tM = to_torch(dev, packed, offsets, M)
-    plain = capi.perm_batched(tp, to, tM, tM)
     tuned = capi.perm_batched(tp, to, tM, tM, opts=dict(exhaustive=1))  # times settings on a sample
     again = capi.perm_batched(tp, to, tM, tM)  # same sizes: the tuned setting is reused
     torch.cuda.synchronize(dev)
     for b in range(len(sizes)):
         n = int(sizes[b])
         A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
-        ref = capi.value(plain, capi.PERM_C128, b)
-        close(capi.value(tuned, capi.PERM_C128, b), ref, A)
+        if n <= 12 or b % 10 == 0:
+            close(capi.value(tuned, capi.PERM_C128, b), oracle.glynn(A), A)
+        # the replayed graph with the kept setting computes the same sums in the same order
         assert capi.value(again, capi.PERM_C128, b) == capi.value(tuned, capi.PERM_C128, b)

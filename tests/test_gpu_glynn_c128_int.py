@@ -78,6 +78,27 @@ def test_all_ones_factorial_exact(capi, dev, n):
     assert run(capi, "perm_glynn", np.ones((m, n), dtype=np.uint8), dev) == math.factorial(n) // math.factorial(n - m)
 
 
+@pytest.mark.parametrize("m,n", [(1, 24), (3, 24), (8, 24), (10, 26), (17, 18)])
+def test_grouped_rectangular_exact(capi, dev, m, n):
+    # the grouped rectangular walk (2^(m-1) (n-m+1) terms with binomial weights), exact
+    # modulo 2^128, against the oracle's rectangular Ryser in exact 128-bit integers.
+    # Host buffers: an input whose 2^(n-1) (n-m)! per(A) may leave int128 raises.
+    A = inputs.rng(5150 + 7 * m + n).integers(-3, 4, (m, n)).astype(np.int64)
+    out = np.zeros(2, dtype=np.int64)
+    capi.perm_glynn(A, out=out)
+    assert capi.value(out, capi.PERM_I64) == oracle.ryser_rect(A)
+    B = inputs.bernoulli01(m, n, 5160 + m + n, 0.5)
+    assert run(capi, "perm_glynn", B, dev) == oracle.ryser_rect(B.astype(np.int64))
+
+
+def test_grouped_rectangular_outside_int128_is_refused(capi, dev):
+    # 2^39 (40-6)! exceeds 2^127 by itself: no exact int128 result exists
+    A = inputs.rng(5170).integers(-3, 4, (6, 40)).astype(np.int64)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_glynn(A, out=np.zeros(2, dtype=np.int64))
+    assert e.value.status == capi.PERM_EOVERFLOW
+
+
 @pytest.mark.parametrize("n", [4, 9, 14])
 def test_int64_exact(capi, dev, n):
     A = inputs.rng(5200 + n).integers(-50, 51, (n, n)).astype(np.int64)
@@ -145,3 +166,13 @@ def test_complex_integer_pipes_haar_and_partial(capi, dev):
     got = complex(o[0] + o[1], o[2] + o[3])
     ref = oracle.glynn_partial(B, 100, 900)
     assert abs(got - ref) <= 1e-12 * 800 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("m,n", [(1, 30), (3, 30), (6, 40), (9, 22), (20, 21)])
+def test_complex_grouped_rectangle(capi, dev, m, n):
+    # the grouped rectangular walk on the integer pipes (default for complex n >= 10):
+    # 2^(m-1) (n-m+1) terms with binomial weights, against the oracle's rectangular Ryser
+    A = inputs.complex_gaussian(m, n, 4700 + 13 * m + n)
+    ref = oracle.ryser_rect(A)
+    close(run(capi, "perm_glynn", A, dev), ref, A)
+    close(run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev, dict(arith=2)), ref, A)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import U, close, device, run, term_bound, to_dev
+from gpu_util import U, close, device, read_golden, run, term_bound, to_dev
 from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -98,3 +98,110 @@ def test_fixed_nonfinite_input_gives_nan(capi, dev):
     A = inputs.uniform_real(6, 6, 7501)
     A[2, 2] = np.inf
     assert math.isnan(run(capi, "perm_glynn", A, dev, FIXED))
+
+
+# ---------------------------------------------------------------- mixed arithmetic
+MIXED = dict(arith=3)
+
+
+@pytest.mark.parametrize("n", [10, 13, 16, 19, 21])
+def test_mixed_square(capi, dev, n):
+    # the last 4 columns of each term multiplied on the FP64 unit (2^-53 per factor)
+    A = inputs.uniform_real(n, n, 7600 + n)
+    close(run(capi, "perm_glynn", A, dev, MIXED), oracle.glynn(A), A, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [26, 30, 34])
+def test_mixed_sampled_partials(capi, dev, n):
+    # padded orders 28, 32, 36: 4, 6 and 8 columns on the FP64 unit; sampled term
+    # ranges (ragged ends, a range crossing a chunk boundary) against the oracle
+    import torch
+    A = inputs.uniform_real(n, n, 7650 + n)
+    T = 1 << (n - 1)
+    K = {26: 4, 30: 6, 34: 8}[n]
+    for a, b in ((0, 3000), (T // 3 + 5, T // 3 + 5000), (T - 2049, T)):
+        out = capi.perm_glynn_partial(to_dev(A, dev), a, b, opts=MIXED)
+        torch.cuda.synchronize(dev)
+        got = capi.dd_value(out)
+        ref = oracle.glynn_partial(A, a, b)
+        scale = oracle.glynn_partial_abs(A, a, b)
+        assert abs(got - ref) <= max(1e-13 * abs(ref), ((n - K + 5) * 2.0 ** -60 + 2 * K * 2.0 ** -53) * scale)
+
+
+def test_mixed_is_default_and_error_bound_holds(capi, dev):
+    import torch
+    A = inputs.uniform_real(22, 22, 7701)
+    ref = oracle.glynn(A)
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(err=err))
+    torch.cuda.synchronize(dev)
+    got = capi.value(out, capi.PERM_F64)
+    assert abs(got - ref) <= float(err.item()) + 2 * U * abs(ref)
+    assert got == run(capi, "perm_glynn", A, dev, MIXED)
+
+
+def test_mixed_sampled_n36_against_oracle_partials(capi, dev):
+    import torch
+    A = inputs.square36_f64()
+    T = 1 << 35
+    for a in (4096, T // 2 + 12345, T - 8192):
+        out = capi.perm_glynn_partial(to_dev(A, dev), a, a + 4096, opts=MIXED)
+        torch.cuda.synchronize(dev)
+        got = capi.dd_value(out)
+        ref = oracle.glynn_partial(A, a, a + 4096)
+        scale = oracle.glynn_partial_abs(A, a, a + 4096)
+        # 28 integer columns (< 2^-60 per column) and 8 on the FP64 unit (2 x 2^-53 each)
+        assert abs(got - ref) <= max(1e-13 * abs(ref), (33 * 2.0 ** -60 + 16 * 2.0 ** -53) * scale)
+
+
+# ------------------------------------------------- grouped rectangular walk (m < n)
+@pytest.mark.parametrize("m,n", [(1, 2), (1, 12), (2, 11), (3, 30), (5, 13), (9, 20), (12, 17), (4, 64),
+                                 (15, 16), (11, 44), (16, 33)])
+@pytest.mark.parametrize("arith", [2, 3])
+def test_grouped_rectangle_against_oracle(capi, dev, m, n, arith):
+    # 2^(m-1) (n-m+1) grouped terms instead of 2^(n-1); the oracle's grouped sum is
+    # pinned against its ungrouped Glynn, Ryser and the definition on small shapes
+    A = inputs.uniform_real(m, n, 7800 + 67 * m + n)
+    ref = oracle.glynn(A) if n <= 20 else oracle.glynn_rect_grouped(A)
+    close(run(capi, "perm_glynn", A, dev, dict(arith=arith)), ref, A, rel=1e-12)
+    close(run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev, dict(arith=arith)), ref, A, rel=1e-12)
+
+
+@pytest.mark.parametrize("m,n", [(1, 40), (3, 17), (6, 40), (20, 40)])
+def test_grouped_rectangle_all_ones(capi, dev, m, n):
+    # all-ones m x n: n! / (n-m)!; the alternating binomial sums cancel completely
+    A = np.ones((m, n))
+    ref = float(math.factorial(n) // math.factorial(n - m))
+    close(run(capi, "perm_glynn", A, dev), ref, A, rel=1e-13)
+
+
+def test_grouped_rectangle_20x40_against_golden(capi, dev):
+    # the 20 x 40 uniform[0,1] workload: 2^19 x 21 grouped terms; value and sum |t| from
+    # the oracle (grouped sum in long double).  The sum cancels (sum|t| / |per| ~ 4e7), so
+    # the tolerance is the stated bound of each side plus the oracle's long-double bound
+    import torch
+    gold = read_golden("rect20x40_f64.txt")
+    A = inputs.rect20x40_f64()
+    assert int(gold["seed"][0]) == inputs.SEED_BASE + 3
+    ref = float(gold["glynn"][0]) + float(gold["glynn"][1])
+    m, n = A.shape
+    norm = 2.0 ** (n - 1) * math.factorial(n - m)
+    scale = float(gold["sum_abs"][0]) / norm
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(err=err))
+    torch.cuda.synchronize(dev)
+    got = capi.value(out, capi.PERM_F64)
+    stated = float(err.item())
+    assert 0.0 < stated <= (n + 5) * 2.0 ** -60 * scale * 1.001
+    oracle_bound = (n + 4) * 2.0 ** -64 * scale
+    assert abs(got - ref) <= stated + oracle_bound + 1e-15 * abs(ref), (got, ref, stated)
+
+
+def test_grouped_rectangle_is_not_used_for_partials(capi, dev):
+    # perm_glynn_partial keeps the ungrouped term index (2^(n-1) Gray-code terms)
+    import torch
+    A = inputs.uniform_real(5, 12, 7901)
+    out = capi.perm_glynn_partial(to_dev(A, dev), 0, 1 << 11, opts=FIXED)
+    torch.cuda.synchronize(dev)
+    total = capi.dd_value(out) / (2.0 ** 11 * math.factorial(7))
+    close(total, oracle.glynn(A), A, rel=1e-13)
