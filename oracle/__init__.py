@@ -271,3 +271,32 @@ def digits_lost(evaluated, true, macheps: float = np.finfo(np.float64).eps) -> f
     if err == 0:
         return -np.inf
     return float(np.log10(err / abs(true)) - np.log10(macheps))
+
+
+def sbp_selection_matrix(occ: int, N: int, n: int) -> np.ndarray:
+    """The N x n selection matrix P of an occupation bitstring (bit j of ``occ`` = m_j,
+    state j occupied): P[j, k] = 1 when m_j = 1 and j is the k-th occupied state
+    (Eq. SBGpermanent and the definition of p that precedes it).  Raises unless exactly
+    n states are occupied."""
+    P = np.zeros((N, n), dtype=np.int64)
+    k = 0
+    for j in range(N):
+        if (occ >> j) & 1:
+            if k == n:
+                raise ValueError("more than n occupied states")
+            P[j, k] = 1
+            k += 1
+    if k != n:
+        raise ValueError("fewer than n occupied states")
+    return P
+
+
+def sbp_coefficient(C, occ: int, prec: str = "ld"):
+    """Coefficient of the occupation bitstring ``occ`` in the symmetric product of
+    bosons built from the n x N coefficient matrix C (Eq. SBP): c_m = per(C P), with P
+    the selection matrix above (Eq. SBGpermanent).  C P is formed by a matrix product."""
+    C = np.asarray(C)
+    n, N = C.shape
+    P = sbp_selection_matrix(int(occ), N, n)
+    M = C @ P.astype(C.dtype)
+    return glynn(M, prec)

@@ -407,3 +407,33 @@ def test_grouped_glynn_invariants(m, n):
     lhs = oracle.glynn_rect_grouped(S)
     rhs = oracle.glynn_rect_grouped(B) + 3.0 * oracle.glynn_rect_grouped(C)
     assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), 1.0)
+
+
+# ------------------------------------------- SBP coefficients (Eq. SBGpermanent)
+@pytest.mark.parametrize("n,N", [(2, 5), (3, 7), (4, 8)])
+def test_sbp_coefficients_sum_to_rectangular_permanent(n, N):
+    # every injective map rows -> states has an image of n states, so summing per(C P)
+    # over all n-subsets gives the rectangular permanent (Eq. rectangular_permanent_definition)
+    g = inputs.rng(200 + n + N)
+    C = g.integers(-3, 4, (n, N))
+    total = 0
+    for S in itertools.combinations(range(N), n):
+        total += oracle.sbp_coefficient(C, sum(1 << j for j in S))
+    assert total == oracle.definition(C)
+
+
+def test_sbp_selection_matrix_and_closed_forms():
+    P = oracle.sbp_selection_matrix(0b1011001, 7, 4)
+    assert P.sum(axis=0).tolist() == [1, 1, 1, 1]  # one state per boson
+    assert P.sum(axis=1).tolist() == [1, 0, 0, 1, 1, 0, 1]  # row sums are the occupations m_j
+    assert [int(np.argmax(P[:, k])) for k in range(4)] == [0, 3, 4, 6]  # in increasing order
+    with pytest.raises(ValueError):
+        oracle.sbp_selection_matrix(0b111, 7, 4)
+    # all-ones coefficients: every coefficient is n!
+    assert oracle.sbp_coefficient(np.ones((5, 9), dtype=np.int64), 0b110110001) == math.factorial(5)
+    # rank one C = u v^T: c_m = n! prod(u) prod_{j occupied} v_j
+    g = inputs.rng(210)
+    u, v = g.uniform(0.5, 1.5, 4), g.uniform(0.5, 1.5, 10)
+    occ = 0b1001010010
+    expect = math.factorial(4) * float(np.prod(u)) * float(np.prod([v[j] for j in range(10) if (occ >> j) & 1]))
+    assert _rel(oracle.sbp_coefficient(np.outer(u, v), occ), expect) < 1e-13
