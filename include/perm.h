@@ -135,6 +135,21 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
 int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                  int64_t count, int dtype, void* out, void* stream, const perm_opts* opts);
 
+/* Coefficients of a symmetric product of bosons (Eq. SBP): for each occupation
+ * bitstring occ[k] (bit j set = state j occupied, exactly n states occupied, all
+ * below bit N), out[k] = c_m = per(C P) (Eq. SBGpermanent), the permanent of the
+ * n x n matrix formed by the occupied columns of C in increasing order.  C is n x N,
+ * row-major with leading dimension ld >= N (elements of `dtype`, PERM_F64 or
+ * PERM_C128); n <= 32, N <= 64.  The columns are gathered inside the kernel; no
+ * submatrix is materialised.  C, occ and out may each be device or host memory; out
+ * receives `count` results (double, or (re, im) pairs).  A bitstring with the wrong
+ * number of occupied states gets NaN.  FP64 arithmetic with compensated sums;
+ * opts->chunk_log2 sets the rebuild interval of the column sums (default 14).
+ * Errors: PERM_EINVAL (shapes, null pointers), PERM_ETOOBIG (n > 32 or N > 64),
+ * PERM_EUNSUPPORTED (integer dtypes). */
+int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,
+             int64_t count, void* out, void* stream, const perm_opts* opts);
+
 /* Unnormalised partial Glynn sum over the terms g_begin <= g < g_end of Eq. glynn_rectangle:
  *     sum_g (-1)^g prod_j ( sum_{i<m} delta_i(g) a_ij + sum_{i>=m} delta_i(g) ),
  * where delta_i(g) = -1 if bit (n-1-i) of gray(g) = g ^ (g >> 1) is set, else +1,

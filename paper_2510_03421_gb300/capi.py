@@ -26,7 +26,7 @@ PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
            "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status",
            "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
-           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial")
+           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp")
 PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
 PERM_NCAND = 4
 PERM_NFEATURES = 12
@@ -66,6 +66,7 @@ def lib():
             L.perm_glynn_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_ryser_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_sbp.argtypes = [vp, vp, i64, i64, i64, i32, vp, i64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
             L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
             fp = ctypes.c_void_p
@@ -264,6 +265,20 @@ def perm_batched(packed, offsets, M, N, out=None, stream=None, opts=None):
                             _ptr(out), _stream(dev, stream), _opts(opts))
     if rc:
         raise PermError(rc, "perm_batched")
+    return out
+
+
+def perm_sbp(C, occ, out=None, stream=None, opts=None):
+    """SBP coefficients: out[k] = per of the n x n matrix of the occupied columns of the
+    n x N matrix C (bit j of occ[k] = state j occupied); occ is a uint64 array/tensor."""
+    keep, p, n, N, ld, code, dev = _matrix(C)
+    count = len(occ)
+    if out is None:
+        out = _out_like(code, dev, count)
+    rc = lib().perm_sbp(handle(_device_index(dev)), p, n, N, ld, code, _ptr(occ), count, _ptr(out),
+                        _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_sbp")
     return out
 
 

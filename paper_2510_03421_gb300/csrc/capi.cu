@@ -727,6 +727,8 @@ int run_candidate(Call& c, int cand) {
 
 uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDefaultMaxTerms; }
 
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
 }  // namespace
 }  // namespace perm
 
@@ -780,6 +782,7 @@ int perm_destroy(perm_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   if (h->ws) cudaFree(h->ws);
+  if (h->sws) cudaFree(h->sws);
   batched_release(h);
   delete h;
   return PERM_OK;
@@ -992,6 +995,65 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
   if (!h) return PERM_EINVAL;
   if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
   return batched_run(h, packed, offsets, M, N, count, dtype, out, static_cast<cudaStream_t>(stream), opts);
+}
+
+int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,
+             int64_t count, void* out, void* stream, const perm_opts* opts) {
+  if (!h) return PERM_EINVAL;
+  if (dtype == PERM_U8 || dtype == PERM_I64) return PERM_EUNSUPPORTED;
+  if (dtype != PERM_F64 && dtype != PERM_C128) return PERM_EINVAL;
+  if (count < 0 || n < 1 || N < n || ld < N) return PERM_EINVAL;
+  if (count > 0 && (!C || !occ || !out)) return PERM_EINVAL;
+  if (n > 32 || N > 64) return PERM_ETOOBIG;
+  const int chunk = (opts && opts->chunk_log2) ? opts->chunk_log2 : 14;
+  if (chunk < 1 || chunk > 62) return PERM_EINVAL;
+  if (count == 0) return PERM_OK;
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t W = dtype == PERM_C128 ? 2 : 1;
+  const size_t c_bytes = 8 * W * (size_t)((n - 1) * ld + N);
+  const bool hC = !on_device(C), hOcc = !on_device(occ), hOut = !on_device(out);
+  const size_t need = (hC ? align_up(c_bytes) : 0) + (hOcc ? align_up(8 * (size_t)count) : 0) +
+                      (hOut ? align_up(8 * W * (size_t)count) : 0);
+  if (need > h->sws_bytes) {
+    if (h->sws) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return PERM_ECUDA;
+      cudaFree(h->sws);
+      h->sws = nullptr;
+      h->sws_bytes = 0;
+    }
+    if (cudaMalloc(&h->sws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return PERM_ENOMEM;
+    }
+    h->sws_bytes = need;
+  }
+  char* base = static_cast<char*>(h->sws);
+  const double* dC = static_cast<const double*>(C);
+  const uint64_t* dOcc = occ;
+  double* dOut = static_cast<double*>(out);
+  if (hC) {
+    if (cudaMemcpyAsync(base, C, c_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dC = reinterpret_cast<const double*>(base);
+    base += align_up(c_bytes);
+  }
+  if (hOcc) {
+    if (cudaMemcpyAsync(base, occ, 8 * (size_t)count, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dOcc = reinterpret_cast<const uint64_t*>(base);
+    base += align_up(8 * (size_t)count);
+  }
+  if (hOut) dOut = reinterpret_cast<double*>(base);
+  const int rc = sbp_run(h, dC, ld, (int)n, (int)N, dtype, dOcc, count, dOut, s, chunk, h->sms);
+  if (rc == 1) return PERM_ETOOBIG;
+  if (rc) return PERM_ECUDA;
+  if (hOut) {
+    if (cudaMemcpyAsync(out, dOut, 8 * W * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PERM_ECUDA;
+  }
+  if (hC || hOcc || hOut) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
 }  // extern "C"

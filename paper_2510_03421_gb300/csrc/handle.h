@@ -39,6 +39,9 @@ struct perm_handle_s {
   perm::BatchTune tune;
   bool tuned = false;
   uint64_t tuned_hist = 0;      // size histogram the tune was chosen for
+  // staging of perm_sbp operands given in host memory
+  void* sws = nullptr;
+  size_t sws_bytes = 0;
   // cost model of perm_auto (host copy of the weights)
   std::vector<float> model;
   int model_in = 0, model_hid = 0, model_out = 0;

@@ -1,0 +1,102 @@
+"""Parity of perm_sbp (SBP coefficients c_m = per(C P), Eq. SBGpermanent) with the
+CPU oracle, which forms C P by a matrix product with the selection matrix."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import close, device
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+def bits(cols):
+    return sum(1 << j for j in cols)
+
+
+def sample_occ(g, n, N, count):
+    return np.array([bits(sorted(g.choice(N, n, replace=False))) for _ in range(count)], dtype=np.uint64)
+
+
+def coef(capi, out, code, k):
+    return capi.value(out, code, k)
+
+
+def test_real_all_bitstrings_lane_items(capi, dev):
+    import torch
+    g = inputs.rng(9900)
+    n, N = 6, 14
+    C = g.uniform(-1, 1, (n, N))
+    occ = np.array([bits(S) for S in itertools.combinations(range(N), n)], dtype=np.uint64)
+    out = capi.perm_sbp(torch.from_numpy(C).to(dev), torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    for k in range(0, len(occ), 7):
+        M = C[:, [j for j in range(N) if (int(occ[k]) >> j) & 1]]
+        close(got[k], oracle.sbp_coefficient(C, int(occ[k])), M)
+    # every injective map rows -> states has one image: the coefficients sum to the
+    # rectangular permanent of C
+    close(float(np.sum(got)), oracle.glynn_rect_grouped(C), C, rel=1e-11)
+
+
+@pytest.mark.parametrize("n,N", [(10, 20), (16, 40)])
+def test_complex_sampled_lane_items(capi, dev, n, N):
+    import torch
+    g = inputs.rng(9910 + n)
+    C = (g.standard_normal((n, N)) + 1j * g.standard_normal((n, N))) / np.sqrt(2 * n)
+    occ = sample_occ(g, n, N, 200)
+    out = capi.perm_sbp(torch.from_numpy(C).to(dev), torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    for k in range(0, len(occ), 10 if n > 12 else 1):
+        M = C[:, [j for j in range(N) if (int(occ[k]) >> j) & 1]]
+        close(coef(capi, out, capi.PERM_C128, k), oracle.sbp_coefficient(C, int(occ[k]), "f64" if n > 12 else "ld"), M)
+
+
+@pytest.mark.parametrize("n,N,kind", [(18, 24, "real"), (20, 26, "complex"), (21, 30, "real")])
+def test_warp_items(capi, dev, n, N, kind):
+    import torch
+    g = inputs.rng(9920 + n)
+    if kind == "real":
+        C = g.uniform(-1, 1, (n, N))
+        code = capi.PERM_F64
+    else:
+        C = (g.standard_normal((n, N)) + 1j * g.standard_normal((n, N))) / np.sqrt(2 * n)
+        code = capi.PERM_C128
+    occ = sample_occ(g, n, N, 40)
+    out = capi.perm_sbp(torch.from_numpy(C).to(dev), torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    for k in range(0, len(occ), 13):
+        M = C[:, [j for j in range(N) if (int(occ[k]) >> j) & 1]]
+        close(coef(capi, out, code, k), oracle.sbp_coefficient(C, int(occ[k]), "f64"), M)
+
+
+def test_host_buffers_bad_bitstrings_and_errors(capi, dev):
+    g = inputs.rng(9930)
+    n, N = 5, 11
+    C = g.uniform(-1, 1, (n, N))
+    occ = np.array([bits([0, 2, 4, 6, 8]), bits([0, 1, 2]), bits([1, 3, 5, 7, 9, 10]),
+                    bits([0, 1, 2, 3, 11]), bits([6, 7, 8, 9, 10])], dtype=np.uint64)
+    out = capi.perm_sbp(C, occ)  # numpy in, numpy out
+    assert isinstance(out, np.ndarray)
+    close(out[0], oracle.sbp_coefficient(C, int(occ[0])), C[:, [0, 2, 4, 6, 8]])
+    close(out[4], oracle.sbp_coefficient(C, int(occ[4])), C[:, [6, 7, 8, 9, 10]])
+    assert np.isnan(out[1]) and np.isnan(out[2]) and np.isnan(out[3])  # 3, 6 states; a state >= N
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_sbp(np.ones((33, 40)), occ)
+    assert e.value.status == capi.PERM_ETOOBIG
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_sbp(np.ones((3, 5), dtype=np.uint8), occ)
+    assert e.value.status == capi.PERM_EUNSUPPORTED
