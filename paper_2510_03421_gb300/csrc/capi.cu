@@ -675,6 +675,83 @@ int density_of(const Call& c, double* d) {
   return PERM_OK;
 }
 
+// The m x n operand as a contiguous host array (elements of c.dtype).
+int host_matrix(const Call& c, std::vector<unsigned char>& out) {
+  const size_t es = elem_size(c.dtype);
+  out.assign((size_t)c.m * c.n * es, 0);
+  if (c.m == 0 || c.n == 0) return PERM_OK;
+  const int64_t span = (int64_t)(c.m - 1) * c.rs + (int64_t)(c.n - 1) * c.cs + 1;
+  std::vector<unsigned char> raw((size_t)span * es);
+  if (cudaMemcpyAsync(raw.data(), c.dA, raw.size(), cudaMemcpyDefault, c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  for (int i = 0; i < c.m; ++i)
+    for (int j = 0; j < c.n; ++j)
+      std::memcpy(out.data() + ((size_t)i * c.n + j) * es, raw.data() + (size_t)(i * c.rs + j * c.cs) * es, es);
+  return PERM_OK;
+}
+
+bool nonzero(const unsigned char* e, int dtype) {
+  if (dtype == PERM_F64 || dtype == PERM_C128) {
+    double v[2] = {0.0, 0.0};
+    std::memcpy(v, e, elem_size(dtype));
+    return v[0] != 0.0 || v[1] != 0.0;
+  }
+  bool nz = false;
+  for (size_t b = 0; b < elem_size(dtype); ++b) nz |= e[b] != 0;
+  return nz;
+}
+
+// Structure of the nonzero pattern: the connected components of the bipartite graph
+// rows <-> columns.  A term of the permanent maps every row into its own component,
+// so per(A) is the product of the components' permanents, and it is zero when a row
+// is empty or a component has more rows than columns.
+struct Blocks {
+  bool zero = false;
+  std::vector<std::vector<int>> rows, cols;  // components that contain rows
+};
+
+Blocks find_blocks(const std::vector<unsigned char>& host, int m, int n, int dtype) {
+  Blocks B;
+  const size_t es = elem_size(dtype);
+  std::vector<int> parent(m + n);
+  for (int v = 0; v < m + n; ++v) parent[v] = v;
+  auto find = [&](int v) {
+    while (parent[v] != v) v = parent[v] = parent[parent[v]];
+    return v;
+  };
+  for (int i = 0; i < m; ++i) {
+    bool any = false;
+    for (int j = 0; j < n; ++j)
+      if (nonzero(host.data() + ((size_t)i * n + j) * es, dtype)) {
+        any = true;
+        const int a = find(i), b = find(m + j);
+        if (a != b) parent[a] = b;
+      }
+    if (!any) {
+      B.zero = true;
+      return B;
+    }
+  }
+  std::vector<int> id(m + n, -1);
+  for (int i = 0; i < m; ++i) {
+    const int r = find(i);
+    if (id[r] < 0) {
+      id[r] = (int)B.rows.size();
+      B.rows.emplace_back();
+      B.cols.emplace_back();
+    }
+    B.rows[id[r]].push_back(i);
+  }
+  for (int j = 0; j < n; ++j) {
+    const int r = find(m + j);
+    if (id[r] >= 0) B.cols[id[r]].push_back(j);
+  }
+  for (size_t k = 0; k < B.rows.size(); ++k)
+    if (B.rows[k].size() > B.cols[k].size()) B.zero = true;
+  return B;
+}
+
 // Candidate choice: the model's argmin over feasible candidates, or the built-in rule.
 int choose(perm_handle h, int m, int n, double density, int dtype, uint64_t cap, int* cand, float* pred) {
   bool ok[PERM_NCAND];
@@ -915,6 +992,59 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
   rc = density_of(c, &density);
   if (rc) return rc;
   const uint64_t cap = max_terms(c.o);
+  if (!c.o.exhaustive && density < 1.0) {
+    // structure of the nonzero pattern: an empty row, or independent blocks
+    std::vector<unsigned char> host;
+    if ((rc = host_matrix(c, host)) != PERM_OK) return rc;
+    const Blocks B = find_blocks(host, c.m, c.n, dtype);
+    const bool floating = dtype == PERM_F64 || dtype == PERM_C128;
+    if (B.zero && floating) {
+      if (launch_block_product(dtype, nullptr, 0, c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+      if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+      return finish(c, out_size(dtype));
+    }
+    if (floating && B.rows.size() > 1) {
+      // gather the blocks into the staging area (the operand is no longer needed there)
+      const size_t es = elem_size(dtype);
+      std::vector<unsigned char> packed;
+      std::vector<size_t> at;
+      for (size_t k = 0; k < B.rows.size(); ++k) {
+        at.push_back(packed.size());
+        for (int i : B.rows[k])
+          for (int j : B.cols[k]) {
+            const unsigned char* e = host.data() + ((size_t)i * c.n + j) * es;
+            packed.insert(packed.end(), e, e + es);
+          }
+      }
+      char* ws = static_cast<char*>(h->ws);
+      if (cudaMemcpyAsync(ws, packed.data(), packed.size(), cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
+        return PERM_ECUDA;
+      double* slots = reinterpret_cast<double*>(ws + kStageA + 256);  // 16 bytes per block
+      for (size_t k = 0; k < B.rows.size(); ++k) {
+        Call cb = c;
+        cb.m = (int)B.rows[k].size();
+        cb.n = (int)B.cols[k].size();
+        cb.rs = cb.n;
+        cb.cs = 1;
+        cb.dA = ws + at[k];
+        cb.dOut = slots + 2 * k;
+        cb.dErr = nullptr;
+        cb.hOut = nullptr;
+        cb.hErr = nullptr;
+        int cand = 0;
+        double dk = 0.0;
+        size_t nz = 0;
+        for (size_t b = 0; b < (size_t)cb.m * cb.n; ++b) nz += nonzero(packed.data() + at[k] + b * es, dtype);
+        dk = (double)nz / ((double)cb.m * cb.n);
+        if ((rc = choose(h, cb.m, cb.n, dk, dtype, cap, &cand, nullptr)) != PERM_OK) return rc;
+        if ((rc = run_candidate(cb, cand)) != PERM_OK) return rc;
+      }
+      if (launch_block_product(dtype, slots, (int)B.rows.size(), c.dOut, c.stream) != cudaSuccess) return PERM_ECUDA;
+      if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
+      // the packed blocks are pageable host memory: the copy above completed on return
+      return finish(c, out_size(dtype));
+    }
+  }
   int cand = 0;
   if (c.o.exhaustive) {
     // time every feasible candidate, then run the fastest last so `out` holds its result

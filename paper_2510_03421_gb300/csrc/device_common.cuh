@@ -36,6 +36,13 @@ __device__ __forceinline__ dd dd_add(dd a, dd b) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// (hi + lo) * d for a double d (TwoProd by FMA), about 2^-104 relative error.
+__device__ __forceinline__ dd dd_mul_d(dd a, double d) {
+  const double p = __dmul_rn(a.hi, d);
+  const double e = __fma_rn(a.hi, d, -p);
+  return fast_two_sum(p, __fma_rn(a.lo, d, e));
+}
+
 // (hi + lo) * 2^e, exact barring under/overflow.
 __device__ __forceinline__ dd dd_ldexp(dd a, int e) { return {scalbn(a.hi, e), scalbn(a.lo, e)}; }
 

@@ -181,5 +181,8 @@ cudaError_t launch_write_double(double v, double* p, cudaStream_t s);
 
 // Write a constant result (used for m == 0, per = 1) for a dtype code.
 cudaError_t launch_write_one(int dtype, void* out, cudaStream_t s);
+// out = product of `count` block permanents at slots (16 bytes apart; dtype 0 real,
+// 1 complex), in double-double; count == 0 writes zero
+cudaError_t launch_block_product(int dtype, const double* slots, int count, void* out, cudaStream_t s);
 
 }  // namespace perm

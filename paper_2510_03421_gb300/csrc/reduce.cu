@@ -106,7 +106,39 @@ __global__ void write_one_kernel(int dtype, void* out) {
   }
 }
 
+// Product of `count` block permanents (each a double or a (re, im) pair at slot k,
+// 16 bytes apart) in double-double, or the zero of the dtype when count == 0.
+__global__ void block_product_kernel(int dtype, const double* slots, int count, void* out) {
+  double* o = static_cast<double*>(out);
+  if (count == 0) {
+    o[0] = 0.0;
+    if (dtype == 1) o[1] = 0.0;
+    return;
+  }
+  if (dtype == 0) {
+    dd p{slots[0], 0.0};
+    for (int k = 1; k < count; ++k) p = dd_mul_d(p, slots[2 * k]);
+    o[0] = __dadd_rn(p.hi, p.lo);
+    return;
+  }
+  dd pr{slots[0], 0.0}, pi{slots[1], 0.0};
+  for (int k = 1; k < count; ++k) {
+    const double br = slots[2 * k], bi = slots[2 * k + 1];
+    const dd nr = dd_add(dd_mul_d(pr, br), dd_mul_d(pi, -bi));
+    const dd ni = dd_add(dd_mul_d(pr, bi), dd_mul_d(pi, br));
+    pr = nr;
+    pi = ni;
+  }
+  o[0] = __dadd_rn(pr.hi, pr.lo);
+  o[1] = __dadd_rn(pi.hi, pi.lo);
+}
+
 }  // namespace
+
+cudaError_t launch_block_product(int dtype, const double* slots, int count, void* out, cudaStream_t s) {
+  block_product_kernel<<<1, 1, 0, s>>>(dtype, slots, count, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finish_real(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
                                double* err, bool raw, cudaStream_t s, double sign) {

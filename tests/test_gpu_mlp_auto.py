@@ -140,3 +140,41 @@ def test_model_installs_and_drives_perm_auto(capi, dev):
         assert 0 <= c < capi.PERM_NCAND and np.isfinite(pred[c]) and pred[c] == np.min(pred)
         close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A)
     capi.perm_set_cost_model(None, None)
+
+
+def _block_matrix(g, shapes, complex_=False):
+    """Block-diagonal matrix with the given block shapes, rows and columns permuted."""
+    m = sum(r for r, _ in shapes)
+    n = sum(c for _, c in shapes)
+    A = np.zeros((m, n), dtype=np.complex128 if complex_ else np.float64)
+    i = j = 0
+    for r, c in shapes:
+        B = g.uniform(-1, 1, (r, c))
+        if complex_:
+            B = B + 1j * g.uniform(-1, 1, (r, c))
+        A[i:i + r, j:j + c] = B
+        i += r
+        j += c
+    return A[g.permutation(m)][:, g.permutation(n)]
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_auto_splits_independent_blocks(capi, dev, complex_):
+    # per(A) is the product of the blocks' permanents (each term keeps every row in its
+    # own block); perm_auto finds the blocks of the nonzero pattern
+    g = inputs.rng(9960 + complex_)
+    for shapes in ([(4, 4), (5, 5), (3, 3)], [(4, 6), (5, 5), (3, 4)], [(1, 1), (7, 9), (2, 2)]):
+        A = _block_matrix(g, shapes, complex_)
+        close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A)
+        close(run(capi, "perm_auto", np.ascontiguousarray(A.T), dev), oracle.glynn(A), A)
+
+
+def test_auto_structural_zeros(capi, dev):
+    g = inputs.rng(9970)
+    A = g.uniform(-1, 1, (9, 11))
+    A[4] = 0.0  # an empty row
+    assert run(capi, "perm_auto", A, dev) == 0.0
+    # a block with more rows than columns: no term avoids a zero
+    B = _block_matrix(g, [(5, 3), (4, 8)])
+    assert run(capi, "perm_auto", B, dev) == 0.0
+    assert oracle.glynn(B) == pytest.approx(0.0, abs=1e-12)
