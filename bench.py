@@ -223,7 +223,10 @@ def run_batched(args, dev, stream):
             "terms_per_s": terms / (batched_ms * 1e-3),
             "plain_perms_per_s": count / plain_s, "plain_s": plain_s,
             "speedup_vs_plain": plain_s / (batched_ms * 1e-3),
-            "max_rel_diff_vs_plain": rel, "arith": "fp64 (complex), Kahan-compensated",
+            "max_rel_diff_vs_plain": rel,
+            "arith": "n >= 13: integer pipes (fixed-point column sums, complex software-float products, 192-bit "
+                     "accumulation; the tuner may put part of each product on the FP64 unit); below: FP64, "
+                     "Kahan-compensated",
             "launch": "one CUDA graph (size-class kernels on parallel branches)"}
 
 

@@ -87,8 +87,9 @@ __global__ void batched_cfx_prep_kernel(BatchArgs a, const int32_t* list, int co
 }
 
 // Sum of the Glynn terms [g, g + len) of matrix t (table q, +2q rows of 2n int64),
-// unnormalised, as two 192-bit accumulators scaled by 2^e_lo.
-template <int N>
+// unnormalised, as two 192-bit accumulators scaled by 2^e_lo.  The first K columns of
+// each product are multiplied on the FP64 unit (a complex double, folded in once).
+template <int N, int K>
 __device__ __forceinline__ void cfx_slice(const long long* __restrict__ q, int n, int e_sum, uint64_t g, uint64_t len,
                                           u64 (&ar)[3], u64 (&ai)[3], int& e_lo) {
   long long Sr[N], Si[N];
@@ -134,15 +135,28 @@ __device__ __forceinline__ void cfx_slice(const long long* __restrict__ q, int n
         }
       }
     }
-    // product (pr + i pi) 2^(E - 62), larger component in [2^61, 2^62)
+    // product (pr + i pi) 2^(E - 62), larger component in [2^61, 2^62); columns j < K
+    // as a complex double dr + i di
     long long pr = 0, pi = 0;
     int E = 0;
+    double dr = 1.0, di = 0.0;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      if (j < n) {
+      if (j < K) {
+        const double xr = (double)Sr[j], xi = (double)Si[j];
+        if (j == 0) {
+          dr = xr;
+          di = xi;
+        } else {
+          const double nr = __fma_rn(dr, xr, -__dmul_rn(di, xi));
+          const double ni = __fma_rn(dr, xi, __dmul_rn(di, xr));
+          dr = nr;
+          di = ni;
+        }
+      } else if (j < n) {
         const int l = norm_shift(Sr[j], Si[j]);
         const long long sr = Sr[j] << l, si = Si[j] << l;
-        if (j == 0) {
+        if (j == K) {
           pr = sr;
           pi = si;
           E = 62 - l;
@@ -151,6 +165,7 @@ __device__ __forceinline__ void cfx_slice(const long long* __restrict__ q, int n
         }
       }
     }
+    if (K > 0 && (pr != 0 || pi != 0)) cfold_double(pr, pi, E, dr, di);
     if (pr != 0 || pi != 0) {
       if (g & 1u) {
         pr = -pr;
@@ -193,7 +208,7 @@ __device__ __forceinline__ void write_cplx(const BatchArgs& a, int b, const FxMa
   out[1] = __dadd_rn(vi.hi, vi.lo);
 }
 
-template <int N>
+template <int N, int K>
 __global__ void __launch_bounds__(128) batched_cfx_kernel(BatchArgs a, ClassWork c) {
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -223,7 +238,7 @@ __global__ void __launch_bounds__(128) batched_cfx_kernel(BatchArgs a, ClassWork
     int e_lo = 0;
     dd vr{0.0, 0.0}, vi{0.0, 0.0};
     if (!bad) {
-      cfx_slice<N>(a.fx_table + a.fx_offset[b], t.n, e_sum, g, len, ar, ai, e_lo);
+      cfx_slice<N, K>(a.fx_table + a.fx_offset[b], t.n, e_sum, g, len, ar, ai, e_lo);
       vr = to_dd(ar[0], ar[1], ar[2], e_lo);
       vi = to_dd(ai[0], ai[1], ai[2], e_lo);
     }
@@ -258,24 +273,33 @@ __global__ void __launch_bounds__(128) batched_cfx_kernel(BatchArgs a, ClassWork
   }
 }
 
-void* pick(int npad) {
+// Columns per product on the FP64 unit when the tuner takes the FP64 share: about
+// 3/8 of the padded order (the class's smallest order, npad - 3, exceeds it).
+constexpr int fp64_columns(int npad) { return (3 * npad / 8) & ~1; }
+
+template <int N>
+void* kernel_for(bool share) {
+  return share ? (void*)batched_cfx_kernel<N, fp64_columns(N)> : (void*)batched_cfx_kernel<N, 0>;
+}
+
+void* pick(int npad, bool share) {
   switch (npad) {
-    case 12: return (void*)batched_cfx_kernel<12>;
-    case 16: return (void*)batched_cfx_kernel<16>;
-    case 20: return (void*)batched_cfx_kernel<20>;
-    case 24: return (void*)batched_cfx_kernel<24>;
-    case 28: return (void*)batched_cfx_kernel<28>;
-    case 32: return (void*)batched_cfx_kernel<32>;
+    case 12: return kernel_for<12>(share);
+    case 16: return kernel_for<16>(share);
+    case 20: return kernel_for<20>(share);
+    case 24: return kernel_for<24>(share);
+    case 28: return kernel_for<28>(share);
+    case 32: return kernel_for<32>(share);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-bool batched_cfx_has_class(int npad) { return pick(npad) != nullptr; }
+bool batched_cfx_has_class(int npad) { return pick(npad, false) != nullptr; }
 
-int batched_cfx_blocks_per_sm(int npad, int block) {
-  void* k = pick(npad);
+int batched_cfx_blocks_per_sm(int npad, int block, bool share) {
+  void* k = pick(npad, share);
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
@@ -290,8 +314,8 @@ cudaError_t launch_batched_cfx_prep(const BatchArgs& a, const int32_t* list, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc) {
-  void* k = pick(npad);
+cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc, bool share) {
+  void* k = pick(npad, share);
   if (!k) return cudaErrorInvalidValue;
   BatchArgs args = a;
   ClassWork cw = c;

@@ -224,7 +224,7 @@ int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& a
     lc.block = t.block;
     lc.grid = c.grid;
     lc.stream = br;
-    const cudaError_t e = c.fx ? launch_batched_cfx(args_base, cw, c.npad, lc)
+    const cudaError_t e = c.fx ? launch_batched_cfx(args_base, cw, c.npad, lc, t.fp64_share != 0)
                                : launch_batched_class(args_base, cw, dtype, c.npad, c.lane, lc);
     if (e != cudaSuccess) return PERM_ECUDA;
     if (cudaEventRecord(h->join[k % 16], br) != cudaSuccess) return PERM_ECUDA;
@@ -294,50 +294,53 @@ int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vect
   const int smalls[] = {6, 8, 10, 12};
   const int items[] = {14, 16, 18};
   const int blocks[] = {64, 128};
+  const int shares = fixed ? 2 : 1;  // the FP64 share only exists for the integer-pipe classes
   int rc = PERM_OK;
   for (int ns : smalls)
     for (int il : items)
-      for (int bl : blocks) {
-        BatchTune t = *best;
-        t.n_small = ns;
-        t.item_log2 = il;
-        t.block = bl;
-        Plan p = build_plan(hM, hN, t, fixed, dtype, &sample);
-        for (Plan::Cls& c : p.classes) {
-          const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block)
-                               : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
-          int grid = h->sms * (bps > 0 ? bps : 1);
-          const int need = (c.nitems + t.block / 32 - 1) / (t.block / 32);
-          c.grid = need < grid ? (need > 0 ? need : 1) : grid;
-        }
-        Layout L = layout_of(p, count, start);
-        if ((rc = ensure_bws(h, L.end)) != PERM_OK) goto done;
-        if ((rc = upload_plan(h, p, L, count, s)) != PERM_OK) goto done;
-        {
-          BatchArgs a = base_args;
-          char* base = static_cast<char*>(h->bws);
-          a.order = reinterpret_cast<const int32_t*>(base + L.order);
-          a.part_base = reinterpret_cast<const int32_t*>(base + L.part_base);
-          a.partials = reinterpret_cast<double*>(base + L.partials);
-          a.done = reinterpret_cast<int*>(base + L.done);
-          a.chunk_log2 = t.chunk_log2;
-          set_fx(a, h, L);
-          if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;  // warm-up
-          cudaEventRecord(e0, s);
-          if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;
-          cudaEventRecord(e1, s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = PERM_ECUDA;
-            goto done;
+      for (int bl : blocks)
+        for (int sh = 0; sh < shares; ++sh) {
+          BatchTune t = *best;
+          t.n_small = ns;
+          t.item_log2 = il;
+          t.block = bl;
+          t.fp64_share = sh;
+          Plan p = build_plan(hM, hN, t, fixed, dtype, &sample);
+          for (Plan::Cls& c : p.classes) {
+            const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block, t.fp64_share != 0)
+                                 : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
+            int grid = h->sms * (bps > 0 ? bps : 1);
+            const int need = (c.nitems + t.block / 32 - 1) / (t.block / 32);
+            c.grid = need < grid ? (need > 0 ? need : 1) : grid;
           }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best_ms) {
-            best_ms = ms;
-            *best = t;
+          Layout L = layout_of(p, count, start);
+          if ((rc = ensure_bws(h, L.end)) != PERM_OK) goto done;
+          if ((rc = upload_plan(h, p, L, count, s)) != PERM_OK) goto done;
+          {
+            BatchArgs a = base_args;
+            char* base = static_cast<char*>(h->bws);
+            a.order = reinterpret_cast<const int32_t*>(base + L.order);
+            a.part_base = reinterpret_cast<const int32_t*>(base + L.part_base);
+            a.partials = reinterpret_cast<double*>(base + L.partials);
+            a.done = reinterpret_cast<int*>(base + L.done);
+            a.chunk_log2 = t.chunk_log2;
+            set_fx(a, h, L);
+            if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;  // warm-up
+            cudaEventRecord(e0, s);
+            if ((rc = enqueue(h, p, L, a, dtype, t, count, s)) != PERM_OK) goto done;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+              rc = PERM_ECUDA;
+              goto done;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+              best_ms = ms;
+              *best = t;
+            }
           }
         }
-      }
 done:
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -472,9 +475,12 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     t = best;
   }
 
+  // an explicit arithmetic overrides the tuner's FP64 share: MIXED takes it, FIXED not
+  if (opts && opts->arith == PERM_ARITH_MIXED) t.fp64_share = 1;
+  if (opts && opts->arith == PERM_ARITH_FIXED) t.fp64_share = 0;
   Plan p = build_plan(hM, hN, t, fixed, dtype);
   for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
-    const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block)
+    const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block, t.fp64_share != 0)
                          : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
     const int warps_per_block = t.block / 32;
     int grid = h->sms * (bps > 0 ? bps : 1);
@@ -493,6 +499,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
   key = mix(key, (uint64_t)(uintptr_t)dM);
   key = mix(key, (uint64_t)(uintptr_t)dN);
   key = mix(key, (uint64_t)t.n_small * 1000003ull + t.item_log2 * 1009 + t.chunk_log2 * 31 + t.block);
+  key = mix(key, (uint64_t)t.fp64_share);
   key = mix(key, (uint64_t)(uintptr_t)h->bws);
   key = mix(key, fixed ? 1u : 0u);
 

@@ -201,6 +201,39 @@ __device__ __forceinline__ dd to_dd(u64 a0, u64 a1, u64 a2, int e_lo) {
   return r;
 }
 
+// Fold a complex double d = dr + i di (the FP64 part of a mixed product) into the
+// complex software float (pr + i pi) 2^(E - 62): both components are put on the
+// larger one's exponent as signed integers of at most 53 bits (the smaller loses the
+// bits below that exponent's ulp), normalised, and multiplied in as one factor.
+__device__ __forceinline__ void cfold_double(long long& pr, long long& pi, int& E, double dr, double di) {
+  const u64 br = (u64)__double_as_longlong(dr), bi = (u64)__double_as_longlong(di);
+  const int er = (int)((br >> 52) & 0x7ff), ei = (int)((bi >> 52) & 0x7ff);
+  const int em = er > ei ? er : ei;
+  if (em == 0) {  // the FP64 factor is zero (its columns are integers: no subnormals)
+    pr = 0;
+    pi = 0;
+    return;
+  }
+  // value of component c: (2^52 + frac) 2^(e - 1075) for a normal e; 0 when e == 0
+  const long long mr0 = er ? (long long)((br & ((1ull << 52) - 1)) | (1ull << 52)) : 0;
+  const long long mi0 = ei ? (long long)((bi & ((1ull << 52) - 1)) | (1ull << 52)) : 0;
+  const int shr = em - er, shi = em - ei;
+  long long mr = shr >= 63 ? 0 : (mr0 >> shr), mi = shi >= 63 ? 0 : (mi0 >> shi);
+  if (br >> 63) mr = -mr;
+  if (bi >> 63) mi = -mi;
+  // the factor is (mr + i mi) 2^(em - 1075); normalise it like a column sum
+  const int l = norm_shift(mr, mi);
+  const long long sr = mr << l, si = mi << l;
+  const long long re = __mul64hi(pr, sr) - __mul64hi(pi, si);
+  const long long im = __mul64hi(pr, si) + __mul64hi(pi, sr);
+  const int l2 = norm_shift(re, im);
+  pr = re << l2;
+  pi = im << l2;
+  // (pr + i pi) 2^(E-62) (sr + i si) 2^(em-1075-l) = (re + i im) 2^(E+2+em-1075-l), and
+  // pr' = re << l2 makes the exponent of pr' 2^(E'-62): E' = E + em - 1011 - l - l2
+  E += em - 1011 - l - l2;
+}
+
 // One step of the complex software-float product: (pr + i pi) 2^(E - 62) times the
 // column sum (sr + i si) (already normalised by `l`).
 __device__ __forceinline__ void cmul_step(long long& pr, long long& pi, int& E, long long sr, long long si, int l) {

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
   const int e_sum = tab->e_sum;
   __syncthreads();
   long long* mine = sS + 2 * threadIdx.x;  // column j at mine[2 j T]
+  const int nint = n - a.fp64_cols;        // columns multiplied on the integer pipes (>= 1)
 
   // aligned chunks of 2^chunk_log2 terms, 32 consecutive chunks per warp per round
   const int lane = threadIdx.x & 31;
@@ -121,9 +122,11 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
         const int b = ctz64(g);
         row = (((g >> (b + 1)) & 1u) ? sP : sM) + 2 * (n - 1 - b) * n;
       }
-      // product over the columns, (pr + i pi) 2^(E - 62), larger component in [2^61, 2^62)
+      // product over the columns, (pr + i pi) 2^(E - 62), larger component in [2^61, 2^62);
+      // the last K columns (mixed) on the FP64 unit as a complex double dr + i di
       long long pr = 0, pi = 0;
       int E = 0;
+      double dr = 1.0, di = 0.0;
 #pragma unroll 2
       for (int j = 0; j < n; ++j) {
         long long sr = mine[2 * j * T], si = mine[2 * j * T + 1];
@@ -133,22 +136,26 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
           mine[2 * j * T] = sr;
           mine[2 * j * T + 1] = si;
         }
-        const int l = norm_shift(sr, si);
-        sr <<= l;
-        si <<= l;
-        if (j == 0) {
-          pr = sr;
-          pi = si;
-          E = 62 - l;
+        if (j < nint) {
+          const int l = norm_shift(sr, si);
+          sr <<= l;
+          si <<= l;
+          if (j == 0) {
+            pr = sr;
+            pi = si;
+            E = 62 - l;
+          } else {
+            cmul_step(pr, pi, E, sr, si, l);
+          }
         } else {
-          const long long re = __mul64hi(pr, sr) - __mul64hi(pi, si);
-          const long long im = __mul64hi(pr, si) + __mul64hi(pi, sr);
-          const int l2 = norm_shift(re, im);
-          pr = re << l2;
-          pi = im << l2;
-          E += 64 - l - l2;
+          const double xr = (double)sr, xi = (double)si;  // rounded once (|s| <= 2^61)
+          const double nr = __fma_rn(dr, xr, -__dmul_rn(di, xi));
+          const double ni = __fma_rn(dr, xi, __dmul_rn(di, xr));
+          dr = nr;
+          di = ni;
         }
       }
+      if (nint < n && (pr != 0 || pi != 0)) cfold_double(pr, pi, E, dr, di);
       if (pr != 0 || pi != 0) {
         if (g & 1u) {
           pr = -pr;

@@ -76,7 +76,7 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
 }
 
 template <int N, int K, bool ABS>
-__global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
+__global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   extern __shared__ long long smem_fx[];
   __shared__ dd scratch[2 * 32];
   const int n = a.n;
@@ -210,6 +210,10 @@ void* pick(int n, bool mixed, bool abs) {
 size_t smem_bytes(int n) { return 2u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long); }
 
 }  // namespace
+
+// Threads per block: 192 (two blocks, 12 warps per SM, <= 168 registers) up to N = 36;
+// 128 above (two blocks, 8 warps, <= 255 registers: the column sums no longer fit 168).
+int glynn_fx_block(int n) { return ((n + 3) & ~3) <= 36 ? 192 : 128; }
 
 int glynn_fx_mixed_columns(int n) {
   const int N = (n + 3) & ~3;

@@ -14,6 +14,7 @@ struct BatchTune {
   int item_log2 = 16;    // larger matrices are cut into sub-ranges of <= 2^item_log2 terms
   int chunk_log2 = 14;   // exact rebuild of the column sums every 2^chunk_log2 terms
   int block = 128;       // threads per block of the class kernels
+  int fp64_share = 0;    // complex integer-pipe classes: part of each product on the FP64 unit
 };
 
 struct BatchCache {

@@ -15,8 +15,10 @@ struct SweepArgs {
   uint64_t g_end;     // one past the last term
   int chunk_log2;     // column sums are rebuilt exactly at every multiple of 2^chunk_log2
   int start_mode;     // 1 = per-thread rebuild, 2 = warp DMMA contraction
-  int want_abs;       // integer-pipe sweeps: also accumulate sum |term| (runtime flag)
+  int want_abs = 0;   // integer-pipe sweeps: also accumulate sum |term| (runtime flag)
   void* partials;     // per-block records (layout per kernel family, see below)
+  int fp64_cols = 0;  // complex integer-pipe sweep: the last fp64_cols columns of each
+                      // product on the FP64 unit (0 = none)
 };
 
 struct LaunchCfg {
@@ -56,6 +58,7 @@ cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream
 cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed);
 int glynn_fx_blocks_per_sm(int n, int block, bool mixed);
 int glynn_fx_mixed_columns(int n);
+int glynn_fx_block(int n);  // threads per block of the square kernel (its launch bound)
 // grouped rectangular walk (1 <= m < n; glynn_fxg.cu): g ranges over [0, 2^(m-1)),
 // n - m + 1 terms each
 cudaError_t launch_glynn_fxg(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
@@ -148,10 +151,11 @@ cudaError_t launch_batched_class(const BatchArgs& a, const ClassWork& c, int dty
                                  const LaunchCfg& lc);
 int batched_blocks_per_sm(int dtype, int npad, bool lane, int block);
 // complex warp-item classes on the integer pipes (batched_fx.cu)
+// share: about 3/8 of each product's columns on the FP64 unit (a tuner choice)
 bool batched_cfx_has_class(int npad);
-int batched_cfx_blocks_per_sm(int npad, int block);
+int batched_cfx_blocks_per_sm(int npad, int block, bool share);
 cudaError_t launch_batched_cfx_prep(const BatchArgs& a, const int32_t* list, int count, cudaStream_t stream);
-cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc);
+cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc, bool share);
 }  // namespace perm
 struct perm_handle_s;
 namespace perm {

@@ -88,10 +88,11 @@ def test_haar_blocks_split_items_and_host_buffers(capi, dev):
         assert capi.value(host_out, capi.PERM_C128, b) == got[b]
 
 
-@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("arith", [0, 1, 2, 3])
 def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     # padded orders 16..32 (n = 13..32) are warp items; by default they run on the integer
-    # pipes (batched_fx.cu), with opts.arith = FP64 on the FP64 class kernels.  Square,
+    # pipes (batched_fx.cu), with opts.arith = FP64 on the FP64 class kernels, with MIXED
+    # a share of each product on the FP64 unit, with FIXED without it.  Square,
     # rectangular and transposed shapes, a matrix with a non-finite entry, an empty one.
     import torch
     g = inputs.rng(9650 + arith)

@@ -176,3 +176,27 @@ def test_complex_grouped_rectangle(capi, dev, m, n):
     ref = oracle.ryser_rect(A)
     close(run(capi, "perm_glynn", A, dev), ref, A)
     close(run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev, dict(arith=2)), ref, A)
+
+
+@pytest.mark.parametrize("n", [20, 23])
+@pytest.mark.parametrize("arith", [0, 2, 3])
+def test_complex_fp64_share(capi, dev, n, arith):
+    # from n = 20 the default (and MIXED) complex integer-pipe sweep multiplies 3n/8 of
+    # each product's columns on the FP64 unit; FIXED keeps all on the integer pipes
+    A = inputs.complex_gaussian(n, n, 4800 + n)
+    close(run(capi, "perm_glynn", A, dev, dict(arith=arith)), oracle.glynn(A, prec="f64"), A)
+
+
+def test_complex_fp64_share_sampled_n32(capi, dev):
+    import torch
+    A = inputs.square32_c128()
+    T = 1 << 31
+    for a, b in ((0, 3000), (T // 2 - 1500, T // 2 + 1500), (T - 2999, T)):
+        out = capi.perm_glynn_partial(to_dev(A, dev), a, b)
+        torch.cuda.synchronize(dev)
+        o = out.cpu().numpy()
+        got = complex(o[0] + o[1], o[2] + o[3])
+        ref = oracle.glynn_partial(A, a, b)
+        # 3000 terms of comparable size (no strong cancellation in a random complex
+        # partial sum): 2^-50 relative per term is far inside 1e-12 of the sum
+        assert abs(got - ref) <= 1e-12 * abs(ref)
