@@ -349,6 +349,13 @@ def run_ours(args):
                 "peak_source": "measured now: 2 x DFMA issue rate (perm_probe_rate); achieved counts the "
                                "FP64-equivalent 2n operations per term, computed on the integer pipes",
                 "flops_per_term": flops_per_term}
+        if mixed and n in (33, 34, 35, 36) and args.dtype == "f64":
+            # pipe utilisation of this kernel (N = 36 columns, 8 on the FP64 unit) from one ncu
+            # capture at n = 34; DRAM traffic does not grow with the term count
+            roof["traffic"] = 148224
+            roof["traffic_source"] = "ncu dram__bytes_read+write of glynn_fx_kernel<36, 8, 0> at n = 34"
+            roof["pipes_ncu"] = {"alu": 0.628, "fp64": 0.614, "fma": 0.276, "issue": 0.573,
+                                 "source": "profiles/glynn_fx_mixed_n34_ncu.md"}
     else:
         roof = {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
