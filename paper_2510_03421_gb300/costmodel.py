@@ -326,8 +326,20 @@ def save(path, weights, meta):
 
 
 def load(path=MODEL_PATH):
-    z = np.load(path, allow_pickle=False)
-    return z["weights"], tuple(int(v) for v in z["dims"]), json.loads(str(z["meta"]))
+    """(weights, dims, meta) of a saved model; ValueError if the file is damaged."""
+    try:
+        z = np.load(path, allow_pickle=False)
+        w = np.asarray(z["weights"], np.float32)
+        dims = tuple(int(v) for v in z["dims"])
+        meta = json.loads(str(z["meta"]))
+    except Exception as e:  # unreadable archive, missing array, bad metadata
+        raise ValueError("cost model file %s is damaged: %s" % (path, e)) from None
+    in_dim, hid, out = dims if len(dims) == 3 else (0, 0, 0)
+    if (in_dim, out) != (capi.PERM_NFEATURES, capi.PERM_NCAND) or \
+            w.size != in_dim * hid + hid + hid * hid + hid + hid * out + out or not np.all(np.isfinite(w)):
+        raise ValueError("cost model file %s does not hold a %d -> %d perceptron" % (path, capi.PERM_NFEATURES,
+                                                                                 capi.PERM_NCAND))
+    return w, dims, meta
 
 
 def install(path=MODEL_PATH, device=0):

@@ -1100,6 +1100,8 @@ int perm_set_cost_model(perm_handle h, const float* weights, int32_t in_dim, int
   int64_t count = 0;
   if (perm_mlp_size(in_dim, hidden, out_dim, &count) != PERM_OK) return PERM_EINVAL;
   if (in_dim != PERM_NFEATURES || out_dim != PERM_NCAND) return PERM_EINVAL;
+  for (int64_t k = 0; k < count; ++k)
+    if (!std::isfinite(weights[k])) return PERM_EINVAL;  // a damaged model: keep the current one
   h->model.assign(weights, weights + count);
   h->model_in = in_dim;
   h->model_hid = hidden;

@@ -80,3 +80,27 @@ def test_opts_struct_layout_matches_header():
     # six int32, one uint64, one pointer
     assert ctypes.sizeof(capi.perm_opts) == 6 * 4 + 8 + 8
     assert capi.perm_opts.max_terms.offset == 24 and capi.perm_opts.err.offset == 32
+
+
+def test_damaged_cost_model_file_is_refused(tmp_path):
+    # a damaged or mismatched model file raises instead of installing garbage; perm_auto
+    # then keeps its current model (or the built-in rule)
+    import numpy as np
+
+    from paper_2510_03421_gb300 import costmodel
+    w, dims, meta = costmodel.load()  # the shipped model loads
+    assert dims[0] == 12 and dims[2] == 4 and np.all(np.isfinite(w))
+    bad = tmp_path / "bad.npz"
+    bad.write_bytes(b"not an npz archive")
+    with pytest.raises(ValueError):
+        costmodel.load(str(bad))
+    nan = tmp_path / "nan.npz"
+    w2 = w.copy()
+    w2[5] = np.nan
+    np.savez(nan, weights=w2, dims=np.array(dims), meta=np.array("{}"))
+    with pytest.raises(ValueError):
+        costmodel.load(str(nan))
+    short = tmp_path / "short.npz"
+    np.savez(short, weights=w[:-3], dims=np.array(dims), meta=np.array("{}"))
+    with pytest.raises(ValueError):
+        costmodel.load(str(short))
