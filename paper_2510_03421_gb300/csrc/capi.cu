@@ -362,9 +362,9 @@ int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
     while (k > (grouped ? 0 : 2) && ((g1 - g0) >> k) * per_step < 1024 * warps) --k;
     a.chunk_log2 = k;
   }
-  // unless FIXED is asked for, about 3/8 of the columns of each product go to the FP64
-  // unit (measured: n = 26, 10 columns: +10%; n = 32, 12 columns: +6%)
-  if (!grouped && c.o.arith != PERM_ARITH_FIXED && c.n >= 20) a.fp64_cols = (3 * c.n) / 8;
+  // MIXED: about 3/8 of the columns of each product on the FP64 unit.  Not the default:
+  // +10% / +6% at n = 26 / 32 on uniform entries, -7% on the 32x32 Gaussian workload.
+  if (!grouped && c.o.arith == PERM_ARITH_MIXED && c.n >= 20) a.fp64_cols = (3 * c.n) / 8;
   // 2^40 maximal terms per 192-bit accumulator (2^6 per grouped step)
   if (a.chunk_log2 > (grouped ? 34 : 40)) return PERM_ETOOBIG;
   if (launch_glynn_cfx(a, cfx_table(c.h), lc, grouped) != cudaSuccess) return PERM_ECUDA;

@@ -181,8 +181,8 @@ def test_complex_grouped_rectangle(capi, dev, m, n):
 @pytest.mark.parametrize("n", [20, 23])
 @pytest.mark.parametrize("arith", [0, 2, 3])
 def test_complex_fp64_share(capi, dev, n, arith):
-    # from n = 20 the default (and MIXED) complex integer-pipe sweep multiplies 3n/8 of
-    # each product's columns on the FP64 unit; FIXED keeps all on the integer pipes
+    # from n = 20 MIXED multiplies 3n/8 of each product's columns on the FP64 unit; the
+    # default and FIXED keep all on the integer pipes
     A = inputs.complex_gaussian(n, n, 4800 + n)
     close(run(capi, "perm_glynn", A, dev, dict(arith=arith)), oracle.glynn(A, prec="f64"), A)
 
@@ -192,7 +192,7 @@ def test_complex_fp64_share_sampled_n32(capi, dev):
     A = inputs.square32_c128()
     T = 1 << 31
     for a, b in ((0, 3000), (T // 2 - 1500, T // 2 + 1500), (T - 2999, T)):
-        out = capi.perm_glynn_partial(to_dev(A, dev), a, b)
+        out = capi.perm_glynn_partial(to_dev(A, dev), a, b, opts=dict(arith=3))
         torch.cuda.synchronize(dev)
         o = out.cpu().numpy()
         got = complex(o[0] + o[1], o[2] + o[3])
