@@ -218,9 +218,12 @@ def run_batched(args, dev, stream):
     za, zp = a[:, 0] + 1j * a[:, 1], p[:, 0] + 1j * p[:, 1]
     rel = float(np.max(np.abs(za - zp) / np.maximum(np.abs(zp), 1e-300)))
     terms = float(np.sum(2.0 ** (sizes.astype(np.float64) - 1)))
+    # algorithmic work of the complex Glynn sweep: 8n - 4 FP64-equivalent operations per term
+    flops = float(np.sum(2.0 ** (sizes.astype(np.float64) - 1) * (8.0 * sizes - 4.0)))
     return {"workload": "%d complex128 n x n leading blocks of Haar unitaries (order 64), n uniform in 4..20" % count,
             "perms_per_s": count / (batched_ms * 1e-3), "ms_per_batch": batched_ms,
             "terms_per_s": terms / (batched_ms * 1e-3),
+            "fp64_equiv_tflops": flops / (batched_ms * 1e-3) / 1e12,
             "plain_perms_per_s": count / plain_s, "plain_s": plain_s,
             "speedup_vs_plain": plain_s / (batched_ms * 1e-3),
             "max_rel_diff_vs_plain": rel,
@@ -408,6 +411,7 @@ def run_ours(args):
     if not args.no_batched:
         side = torch.cuda.Stream(dev)
         line["batched"] = run_batched(args, dev, side)
+        line["batched"]["frac_of_fp64_peak"] = line["batched"]["fp64_equiv_tflops"] * 1e12 / peak_flops
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
