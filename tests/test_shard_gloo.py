@@ -67,3 +67,21 @@ def test_single_process_path():
     val = shard.sharded_glynn(A, lambda M, a, b: oracle.glynn_partial(M, a, b, dd=True))
     assert abs(val - oracle.glynn(A)) <= 1e-14 * abs(oracle.glynn(A))
     assert math.isclose(shard.normalise_glynn(shard.combine([(8.0, 0.0)]), 2, 3), 2.0)
+
+
+def test_resume_from_checkpoint(tmp_path):
+    # an interrupted range-by-range sweep resumes from its checkpoint and gives the same
+    # exact sum; a checkpoint of another matrix is refused
+    import oracle
+    A = inputs.uniform_real(9, 12, 4300)
+    part = lambda M, a, b: oracle.glynn_partial(M, a, b, dd=True)  # noqa: E731
+    path = str(tmp_path / "sweep.json")
+    assert shard.resumable_glynn(A, part, path, step_terms=100, stop_after=7) is None
+    assert shard.resumable_glynn(A, part, path, step_terms=100, stop_after=5) is None
+    got = shard.resumable_glynn(A, part, path, step_terms=100)
+    ref = oracle.glynn(A)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+    fresh = shard.resumable_glynn(A, part, str(tmp_path / "fresh.json"), step_terms=333)
+    assert abs(fresh - got) <= 1e-15 * abs(got)  # other cuts: the same terms
+    with pytest.raises(ValueError):
+        shard.resumable_glynn(inputs.uniform_real(9, 12, 4301), part, path)
