@@ -205,3 +205,23 @@ def test_grouped_rectangle_is_not_used_for_partials(capi, dev):
     torch.cuda.synchronize(dev)
     total = capi.dd_value(out) / (2.0 ** 11 * math.factorial(7))
     close(total, oracle.glynn(A), A, rel=1e-13)
+
+
+def test_resumable_sweep_on_the_gpu(capi, dev, tmp_path):
+    # a sweep cut into term ranges through perm_glynn_partial, interrupted and resumed
+    # from its checkpoint, against the oracle
+    import torch
+
+    from paper_2510_03421_gb300 import shard
+    A = inputs.uniform_real(20, 20, 7950)
+    dA = torch.from_numpy(A).to(dev)
+
+    def part(M, a, b):
+        o = capi.perm_glynn_partial(dA, a, b)
+        torch.cuda.synchronize(dev)
+        return float(o[0]), float(o[1])
+
+    path = str(tmp_path / "ck.json")
+    assert shard.resumable_glynn(A, part, path, step_terms=1 << 16, stop_after=3) is None
+    got = shard.resumable_glynn(A, part, path, step_terms=1 << 16)
+    close(got, oracle.glynn(A), A, rel=1e-13)
