@@ -1,6 +1,6 @@
-// Batched Glynn (Eq. glynn, Eq. glynn_rectangle) for complex input on the integer
-// pipes: the warp-item classes of perm_batched (matrices cut into aligned sub-ranges
-// of 2^item_log2 terms, one warp each) with the arithmetic of glynn_cfx.cu.
+// Batched Glynn (Eq. glynn, Eq. glynn_rectangle) on the integer pipes: the warp-item
+// classes of perm_batched (matrices cut into aligned sub-ranges of 2^item_log2 terms,
+// one warp each) with the arithmetic of glynn_cfx.cu (complex) and glynn_fx.cu (real).
 //   * A preparation kernel (one warp per matrix, one lane per column) scales column j
 //     by 2^e_j (sum_i (|re a'_ij| + |im a'_ij|) 2^e_j <= 2^61, the padding rows of ones
 //     included), rounds once to int64 and writes +2q (re, im) for every row, the
@@ -273,6 +273,163 @@ __global__ void __launch_bounds__(128) batched_cfx_kernel(BatchArgs a, ClassWork
   }
 }
 
+// Real input: one warp per matrix, lane j scales column j (sum_i |a'_ij| 2^e_j <= 2^61,
+// the padding rows of ones included) and writes +2q for every row (n rows of n int64).
+__global__ void batched_fxr_prep_kernel(BatchArgs a, const int32_t* list, int count) {
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * (blockDim.x >> 5)) + (threadIdx.x >> 5));
+  if (w >= count) return;
+  const int b = list[w];
+  const FxMat t = fxmat_of(a, b);
+  const int j = lane;
+  int e = 0, bad = 0;
+  if (j < t.n) {
+    double colabs = (double)(t.n - t.m);
+    for (int i = 0; i < t.m; ++i) {
+      const double v = a.packed[t.off + i * t.rs + j * t.cs];
+      if (!isfinite(v)) bad = 1;
+      colabs += fabs(v);
+    }
+    int x = 0;
+    if (colabs > 0.0) frexp(colabs, &x);
+    e = 61 - x;
+    long long* q = a.fx_table + a.fx_offset[b] + j;  // row i at q + n i
+    for (int i = 0; i < t.n; ++i) {
+      const long long v = (i < t.m) ? llrint(ldexp(a.packed[t.off + i * t.rs + j * t.cs], e)) : llrint(ldexp(1.0, e));
+      q[t.n * i] = 2 * v;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, o);
+    bad |= __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) a.fx_esum[b] = bad ? kFxBad : e;
+}
+
+// Real terms [g, g + len) of an order-n matrix (table q, +2q rows of n int64) into one
+// 192-bit accumulator; columns j >= n are the constant 2^31 (their scale is added to
+// e_sum), the last K of the N columns are multiplied on the FP64 unit (soft_product).
+template <int N, int K>
+__device__ __forceinline__ void fxr_slice(const long long* __restrict__ q, int n, int e_sum, uint64_t g, uint64_t len,
+                                          u64 (&acc)[3], int& e_lo) {
+  long long S[N];
+  bool anchored = false;
+  e_lo = 0;
+  acc[0] = acc[1] = acc[2] = 0;
+  const int es = e_sum + 31 * (N - n);
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = 0;
+      for (int i = 0; i < n; ++i) {
+        const bool minus = (gray >> (n - 1 - i)) & 1u;
+        const long long* row = q + n * i;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          if (j < n) {
+            const long long v = __ldg(row + j);
+            S[j] += minus ? -v : v;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) S[j] = (j < n) ? (S[j] >> 1) : (1ll << 31);
+    } else {
+      const int b = ctz64(g);
+      const bool plus = (g >> (b + 1)) & 1u;
+      const long long* row = q + n * (n - 1 - b);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        if (j < n) {
+          const long long v = __ldg(row + j);
+          S[j] += plus ? v : -v;
+        }
+      }
+    }
+    u64 P;
+    int E;
+    unsigned neg;
+    soft_product<N, K>(S, P, E, neg);
+    if (P != 0) {
+      if (!anchored) {
+        e_lo = E - es - kAnchorBit;
+        anchored = true;
+      }
+      int p = E - 63 - es - e_lo;
+      if (p > kMaxLsb) {
+        shr192(acc[0], acc[1], acc[2], p - kMaxLsb);
+        e_lo += p - kMaxLsb;
+        p = kMaxLsb;
+      }
+      acc_add(acc[0], acc[1], acc[2], P, p, neg ^ (unsigned)(g & 1u));
+    }
+  }
+}
+
+__device__ __forceinline__ void write_real(const BatchArgs& a, int b, const FxMat& t, dd v, bool bad) {
+  if (bad) {
+    a.out[b] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  v = normalise_fx(v, t.n, t.m);
+  a.out[b] = __dadd_rn(v.hi, v.lo);
+}
+
+template <int N, int K>
+__global__ void __launch_bounds__(128) batched_fxr_kernel(BatchArgs a, ClassWork c) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(c.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= c.nitems) break;
+    const BatchItem it = c.items[item];
+    const int b = a.order[it.first];
+    const FxMat t = fxmat_of(a, b);
+    if (t.m == 0) {
+      if (lane == 0) a.out[b] = 1.0;
+      continue;
+    }
+    const int e_sum = a.fx_esum[b];
+    const bool bad = e_sum == kFxBad;
+    const uint64_t terms = 1ull << (t.n - 1);
+    uint64_t g0, len0, g, len;
+    split_range(0, terms, (uint64_t)it.parts, (uint64_t)it.count, &g0, &len0);
+    split_range(g0, g0 + len0, 32, (uint64_t)lane, &g, &len);
+    dd v{0.0, 0.0};
+    if (!bad) {
+      u64 acc[3];
+      int e_lo = 0;
+      fxr_slice<N, K>(a.fx_table + a.fx_offset[b], t.n, e_sum, g, len, acc, e_lo);
+      v = to_dd(acc[0], acc[1], acc[2], e_lo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = dd_add(v, shfl_down_dd(v, o));
+    if (lane == 0) {
+      if (it.parts == 1) {
+        write_real(a, b, t, v, bad);
+      } else {
+        double* slot = a.partials + 4 * ((int64_t)a.part_base[b] + it.count);
+        slot[0] = v.hi;
+        slot[1] = v.lo;
+        slot[2] = 0.0;
+        slot[3] = 0.0;
+        __threadfence();
+        const int arrived = atomicAdd(a.done + b, 1);
+        if (arrived == it.parts - 1) {
+          __threadfence();
+          const volatile double* p = a.partials + 4 * (int64_t)a.part_base[b];
+          dd sr{0.0, 0.0};
+          for (int k = 0; k < it.parts; ++k) sr = dd_add(sr, dd{p[4 * k], p[4 * k + 1]});
+          write_real(a, b, t, sr, bad);
+        }
+      }
+    }
+  }
+}
+
 // Columns per product on the FP64 unit when the tuner takes the FP64 share: about
 // 3/8 of the padded order (the class's smallest order, npad - 3, exceeds it).
 constexpr int fp64_columns(int npad) { return (3 * npad / 8) & ~1; }
@@ -280,6 +437,25 @@ constexpr int fp64_columns(int npad) { return (3 * npad / 8) & ~1; }
 template <int N>
 void* kernel_for(bool share) {
   return share ? (void*)batched_cfx_kernel<N, fp64_columns(N)> : (void*)batched_cfx_kernel<N, 0>;
+}
+
+// real: 4 columns (6 from N = 32) on the FP64 unit with the share, as the square sweep
+constexpr int fp64_columns_real(int npad) { return npad >= 32 ? 6 : 4; }
+
+template <int N>
+void* kernel_for_real(bool share) {
+  return share ? (void*)batched_fxr_kernel<N, fp64_columns_real(N)> : (void*)batched_fxr_kernel<N, 0>;
+}
+
+void* pick_real(int npad, bool share) {
+  switch (npad) {
+    case 16: return kernel_for_real<16>(share);
+    case 20: return kernel_for_real<20>(share);
+    case 24: return kernel_for_real<24>(share);
+    case 28: return kernel_for_real<28>(share);
+    case 32: return kernel_for_real<32>(share);
+    default: return nullptr;
+  }
 }
 
 void* pick(int npad, bool share) {
@@ -296,26 +472,32 @@ void* pick(int npad, bool share) {
 
 }  // namespace
 
-bool batched_cfx_has_class(int npad) { return pick(npad, false) != nullptr; }
+bool batched_fx_has_class(int dtype, int npad) {
+  return (dtype == 1 ? pick(npad, false) : pick_real(npad, false)) != nullptr;
+}
 
-int batched_cfx_blocks_per_sm(int npad, int block, bool share) {
-  void* k = pick(npad, share);
+int batched_fx_blocks_per_sm(int dtype, int npad, int block, bool share) {
+  void* k = dtype == 1 ? pick(npad, share) : pick_real(npad, share);
   if (!k) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, 0) != cudaSuccess) return 0;
   return nb;
 }
 
-cudaError_t launch_batched_cfx_prep(const BatchArgs& a, const int32_t* list, int count, cudaStream_t stream) {
+cudaError_t launch_batched_fx_prep(const BatchArgs& a, int dtype, const int32_t* list, int count, cudaStream_t stream) {
   if (count <= 0) return cudaSuccess;
   const int warps_per_block = 4;
   const int grid = (count + warps_per_block - 1) / warps_per_block;
-  batched_cfx_prep_kernel<<<grid, 32 * warps_per_block, 0, stream>>>(a, list, count);
+  if (dtype == 1)
+    batched_cfx_prep_kernel<<<grid, 32 * warps_per_block, 0, stream>>>(a, list, count);
+  else
+    batched_fxr_prep_kernel<<<grid, 32 * warps_per_block, 0, stream>>>(a, list, count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc, bool share) {
-  void* k = pick(npad, share);
+cudaError_t launch_batched_fx(const BatchArgs& a, const ClassWork& c, int dtype, int npad, const LaunchCfg& lc,
+                              bool share) {
+  void* k = dtype == 1 ? pick(npad, share) : pick_real(npad, share);
   if (!k) return cudaErrorInvalidValue;
   BatchArgs args = a;
   ClassWork cw = c;

@@ -50,9 +50,9 @@ struct Plan {
   int64_t fx_elems = 0;            // table size (int64 elements)
 };
 
-// The integer-pipe classes: complex warp items of padded order >= 16.
+// The integer-pipe classes: real and complex warp items of padded order >= 16.
 inline bool fx_class(bool fixed, int dtype, bool lane, int npad) {
-  return fixed && dtype == PERM_C128 && !lane && npad >= 16 && batched_cfx_has_class(npad);
+  return fixed && (dtype == PERM_C128 || dtype == PERM_F64) && !lane && npad >= 16 && batched_fx_has_class(dtype, npad);
 }
 
 // Order of matrix b after the transpose rule.
@@ -131,7 +131,7 @@ Plan build_plan(const std::vector<int32_t>& M, const std::vector<int32_t>& N, co
   for (int32_t b : p.fx_list) {
     const int n = order_of(M[b], N[b]);
     p.fx_offset[b] = p.fx_elems;
-    p.fx_elems += 2 * (int64_t)n * n;
+    p.fx_elems += (dtype == PERM_C128 ? 2 : 1) * (int64_t)n * n;
   }
   // largest class first: it starts the graph's branches
   std::stable_sort(p.classes.begin(), p.classes.end(),
@@ -208,8 +208,8 @@ int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& a
   char* base = static_cast<char*>(h->bws);
   if (cudaMemsetAsync(base + L.done, 0, L.counters + 4 * kClasses - L.done, s) != cudaSuccess) return PERM_ECUDA;
   if (!p.fx_list.empty() &&
-      launch_batched_cfx_prep(args_base, reinterpret_cast<const int32_t*>(base + L.fx_list), (int)p.fx_list.size(),
-                              s) != cudaSuccess)
+      launch_batched_fx_prep(args_base, dtype, reinterpret_cast<const int32_t*>(base + L.fx_list),
+                             (int)p.fx_list.size(), s) != cudaSuccess)
     return PERM_ECUDA;
   if (cudaEventRecord(h->fork, s) != cudaSuccess) return PERM_ECUDA;
   int k = 0;
@@ -224,7 +224,7 @@ int enqueue(perm_handle_s* h, const Plan& p, const Layout& L, const BatchArgs& a
     lc.block = t.block;
     lc.grid = c.grid;
     lc.stream = br;
-    const cudaError_t e = c.fx ? launch_batched_cfx(args_base, cw, c.npad, lc, t.fp64_share != 0)
+    const cudaError_t e = c.fx ? launch_batched_fx(args_base, cw, dtype, c.npad, lc, t.fp64_share != 0)
                                : launch_batched_class(args_base, cw, dtype, c.npad, c.lane, lc);
     if (e != cudaSuccess) return PERM_ECUDA;
     if (cudaEventRecord(h->join[k % 16], br) != cudaSuccess) return PERM_ECUDA;
@@ -307,7 +307,7 @@ int tune_batch(perm_handle_s* h, const std::vector<int32_t>& hM, const std::vect
           t.fp64_share = sh;
           Plan p = build_plan(hM, hN, t, fixed, dtype, &sample);
           for (Plan::Cls& c : p.classes) {
-            const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block, t.fp64_share != 0)
+            const int bps = c.fx ? batched_fx_blocks_per_sm(dtype, c.npad, t.block, t.fp64_share != 0)
                                  : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
             int grid = h->sms * (bps > 0 ? bps : 1);
             const int need = (c.nitems + t.block / 32 - 1) / (t.block / 32);
@@ -426,8 +426,8 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
     start = align256(start + 16 * (size_t)count);
   }
   // room for any plan: order, part_base, done (4 B each per matrix), items and partial slots
-  // complex warp items run on the integer pipes unless FP64 arithmetic is asked for
-  const bool fixed = dtype == PERM_C128 && !(opts && opts->arith == PERM_ARITH_FP64);
+  // warp items of order >= 13 run on the integer pipes unless FP64 arithmetic is asked for
+  const bool fixed = !(opts && opts->arith == PERM_ARITH_FP64);
   rc = ensure_bws(h, start + plan_bound(count, max_parts, fixed ? fx_elems : 0));
   if (rc) return rc;
   char* base = static_cast<char*>(h->bws);
@@ -480,7 +480,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
   if (opts && opts->arith == PERM_ARITH_FIXED) t.fp64_share = 0;
   Plan p = build_plan(hM, hN, t, fixed, dtype);
   for (Plan::Cls& c : p.classes) {  // grid sizes (queried outside any stream capture)
-    const int bps = c.fx ? batched_cfx_blocks_per_sm(c.npad, t.block, t.fp64_share != 0)
+    const int bps = c.fx ? batched_fx_blocks_per_sm(dtype, c.npad, t.block, t.fp64_share != 0)
                          : batched_blocks_per_sm(dtype, c.npad, c.lane, t.block);
     const int warps_per_block = t.block / 32;
     int grid = h->sms * (bps > 0 ? bps : 1);

@@ -140,8 +140,9 @@ struct BatchArgs {
   int* done;                // sub-ranges finished per matrix (zeroed before the launch)
   double* out;              // results (complex: (re, im) pairs)
   int chunk_log2;
-  // integer-pipe classes (batched_fx.cu): quantised +2q tables, n rows of 2n int64 per
-  // matrix at fx_table + fx_offset[b], and the sum of the column exponents
+  // integer-pipe classes (batched_fx.cu): quantised +2q tables, n rows of n (real) or 2n
+  // (complex, (re, im)) int64 per matrix at fx_table + fx_offset[b], and the sum of the
+  // column exponents
   long long* fx_table;
   const int64_t* fx_offset;
   int* fx_esum;
@@ -150,12 +151,13 @@ constexpr int kFxBad = -2147483647 - 1;  // fx_esum of a matrix with a non-finit
 cudaError_t launch_batched_class(const BatchArgs& a, const ClassWork& c, int dtype, int npad, bool lane,
                                  const LaunchCfg& lc);
 int batched_blocks_per_sm(int dtype, int npad, bool lane, int block);
-// complex warp-item classes on the integer pipes (batched_fx.cu)
-// share: about 3/8 of each product's columns on the FP64 unit (a tuner choice)
-bool batched_cfx_has_class(int npad);
-int batched_cfx_blocks_per_sm(int npad, int block, bool share);
-cudaError_t launch_batched_cfx_prep(const BatchArgs& a, const int32_t* list, int count, cudaStream_t stream);
-cudaError_t launch_batched_cfx(const BatchArgs& a, const ClassWork& c, int npad, const LaunchCfg& lc, bool share);
+// warp-item classes on the integer pipes (batched_fx.cu), dtype 0 (real) or 1 (complex);
+// share: part of each product's columns on the FP64 unit (a tuner choice)
+bool batched_fx_has_class(int dtype, int npad);
+int batched_fx_blocks_per_sm(int dtype, int npad, int block, bool share);
+cudaError_t launch_batched_fx_prep(const BatchArgs& a, int dtype, const int32_t* list, int count, cudaStream_t stream);
+cudaError_t launch_batched_fx(const BatchArgs& a, const ClassWork& c, int dtype, int npad, const LaunchCfg& lc,
+                              bool share);
 }  // namespace perm
 struct perm_handle_s;
 namespace perm {

@@ -118,6 +118,35 @@ def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     assert np.isnan(got[-1].real) and np.isnan(got[-1].imag)
 
 
+@pytest.mark.parametrize("arith", [0, 1, 2, 3])
+def test_real_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
+    # real warp items of padded order 16..32 on the integer pipes (batched_fx.cu) by
+    # default, on the FP64 class kernels with opts.arith = FP64; MIXED forces the FP64
+    # share of each product, FIXED forbids it
+    import torch
+    g = inputs.rng(9670 + arith)
+    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (21, 23), (6, 26), (23, 23), (0, 18),
+              (6, 30), (12, 18)]
+    mats = [g.uniform(-1, 1, s) for s in shapes]
+    mats[-1][3, 4] = np.inf
+    packed, offsets, M, N = pack(mats, np.float64)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN, opts=dict(arith=arith))
+    torch.cuda.synchronize(dev)
+    got = results(capi, out, capi.PERM_F64, len(mats))
+    for A, x in zip(mats[:-1], got[:-1]):
+        m, n = sorted(A.shape)
+        if m == 0:
+            assert x == 1.0
+        elif n <= 16:
+            close(x, oracle.glynn(A), A)
+        elif m < n and n >= 21:
+            close(x, oracle.glynn_rect_grouped(A if A.shape[0] <= A.shape[1] else A.T), A)
+        else:
+            close(x, oracle.glynn(A, prec="f64"), A)
+    assert np.isnan(got[-1])
+
+
 def test_graph_replay_sees_new_data(capi, dev):
     import torch
     mats = [inputs.uniform_real(n, n, 9700 + n) for n in (3, 7, 11, 15, 18)]
