@@ -233,6 +233,37 @@ def run_batched(args, dev, stream):
             "launch": "one CUDA graph (size-class kernels on parallel branches)"}
 
 
+def run_batched_real(args, dev, stream):
+    """The same batch shape with real entries (uniform[-1,1]): 100,000 matrices, n uniform in
+    4..20, one tuned perm_batched graph launch per step."""
+    import numpy as np
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    count = args.batch_count
+    g = inputs.rng(inputs.SEED_BASE + 6)
+    sizes = g.integers(4, 21, count).astype(np.int32)
+    offsets = np.zeros(count, np.int64)
+    offsets[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
+    packed = g.uniform(-1.0, 1.0, int(offsets[-1] + int(sizes[-1]) ** 2))
+    tp, to, tM = [torch.from_numpy(x).to(dev) for x in (packed, offsets, sizes)]
+    out = torch.empty(count, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        capi.perm_batched(tp, to, tM, tM, out=out, stream=stream, opts=dict(exhaustive=1))
+        for _ in range(max(1, args.warmup)):
+            capi.perm_batched(tp, to, tM, tM, out=out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            capi.perm_batched(tp, to, tM, tM, out=out, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    return {"workload": "%d float64 n x n matrices, uniform[-1,1], n uniform in 4..20, seed %d" % (
+                count, inputs.SEED_BASE + 6),
+            "perms_per_s": count / (ms * 1e-3), "ms_per_batch": ms}
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
     """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
@@ -412,6 +443,7 @@ def run_ours(args):
         side = torch.cuda.Stream(dev)
         line["batched"] = run_batched(args, dev, side)
         line["batched"]["frac_of_fp64_peak"] = line["batched"]["fp64_equiv_tflops"] * 1e12 / peak_flops
+        line["batched_real"] = run_batched_real(args, dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
