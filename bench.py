@@ -264,6 +264,37 @@ def run_batched_real(args, dev, stream):
             "perms_per_s": count / (ms * 1e-3), "ms_per_batch": ms}
 
 
+def run_sbp(args, dev, stream, count=1000000, n=12, N=24):
+    """SBP coefficients c_m = per(C P) (Eq. SBGpermanent): one real n x N coefficient
+    matrix, `count` random occupation bitstrings with n of N states occupied, one
+    perm_sbp call per step (columns gathered inside the kernel)."""
+    import numpy as np
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    g = inputs.rng(inputs.SEED_BASE + 7)
+    C = g.uniform(-1.0, 1.0, (n, N))
+    cols = np.argsort(g.random((count, N)), axis=1)[:, :n]
+    occ = np.bitwise_or.reduce(np.left_shift(np.uint64(1), cols.astype(np.uint64)), axis=1)
+    dC = torch.from_numpy(C).to(dev)
+    docc = torch.from_numpy(occ.view(np.int64)).to(dev)
+    out = torch.empty(count, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            capi.perm_sbp(dC, docc, out=out, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            capi.perm_sbp(dC, docc, out=out, stream=stream)
+            ev[k][1].record(stream)
+        stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    return {"workload": "%d occupation bitstrings, %d of %d states occupied, real coefficients uniform[-1,1], "
+                        "seed %d" % (count, n, N, inputs.SEED_BASE + 7),
+            "coefficients_per_s": count / (ms * 1e-3), "terms_per_s": count * 2.0 ** (n - 1) / (ms * 1e-3),
+            "ms_per_call": ms}
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
     """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
@@ -444,6 +475,7 @@ def run_ours(args):
         line["batched"] = run_batched(args, dev, side)
         line["batched"]["frac_of_fp64_peak"] = line["batched"]["fp64_equiv_tflops"] * 1e12 / peak_flops
         line["batched_real"] = run_batched_real(args, dev, side)
+        line["sbp"] = run_sbp(args, dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
