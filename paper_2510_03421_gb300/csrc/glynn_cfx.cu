@@ -64,6 +64,7 @@ __global__ void cfx_prep_kernel(SweepArgs a, CfxTable* tab) {
 // so the column loop is a rolled loop over the actual n columns: the kernel body stays
 // small enough for the instruction cache.  The table row update of a step is fused
 // into the product loop.
+template <bool SHARE>
 __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTable* __restrict__ tab) {
   extern __shared__ long long smem_cfx[];
   __shared__ dd scratch[3 * 32];
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
   const int e_sum = tab->e_sum;
   __syncthreads();
   long long* mine = sS + 2 * threadIdx.x;  // column j at mine[2 j T]
-  const int nint = n - a.fp64_cols;        // columns multiplied on the integer pipes (>= 1)
+  const int nint = SHARE ? n - a.fp64_cols : n;  // columns on the integer pipes (>= 1)
 
   // aligned chunks of 2^chunk_log2 terms, 32 consecutive chunks per warp per round
   const int lane = threadIdx.x & 31;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
           mine[2 * j * T] = sr;
           mine[2 * j * T + 1] = si;
         }
-        if (j < nint) {
+        if (!SHARE || j < nint) {
           const int l = norm_shift(sr, si);
           sr <<= l;
           si <<= l;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(128) glynn_cfx_kernel(SweepArgs a, const CfxTa
           di = ni;
         }
       }
-      if (nint < n && (pr != 0 || pi != 0)) cfold_double(pr, pi, E, dr, di);
+      if (SHARE && nint < n && (pr != 0 || pi != 0)) cfold_double(pr, pi, E, dr, di);
       if (pr != 0 || pi != 0) {
         if (g & 1u) {
           pr = -pr;
@@ -351,7 +352,7 @@ size_t smem_bytes(int n, int block) { return (4u * (size_t)n * n + 2u * (size_t)
 int glynn_cfx_max_n() { return 64; }
 
 int glynn_cfx_blocks_per_sm(int m, int n, int block, bool grouped) {
-  const void* k = grouped ? (const void*)glynn_cfxg_kernel : (const void*)glynn_cfx_kernel;
+  const void* k = grouped ? (const void*)glynn_cfxg_kernel : (const void*)glynn_cfx_kernel<false>;
   const size_t smem = grouped ? smem_bytes_grouped(m, n, block) : smem_bytes(n, block);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int nb = 0;
@@ -364,7 +365,8 @@ cudaError_t launch_glynn_cfx(const SweepArgs& a, CfxTable* tab, const LaunchCfg&
   cfx_prep_kernel<<<1, 64, 0, c.stream>>>(a, tab);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const void* k = grouped ? (const void*)glynn_cfxg_kernel : (const void*)glynn_cfx_kernel;
+  const void* k = grouped ? (const void*)glynn_cfxg_kernel
+                          : (a.fp64_cols > 0 ? (const void*)glynn_cfx_kernel<true> : (const void*)glynn_cfx_kernel<false>);
   const size_t smem = grouped ? smem_bytes_grouped(a.m, a.n, c.block) : smem_bytes(a.n, c.block);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
