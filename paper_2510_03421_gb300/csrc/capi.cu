@@ -1146,6 +1146,7 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
   if (count == 0) return PERM_OK;
   if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc0 = PERM_OK;
   const size_t W = dtype == PERM_C128 ? 2 : 1;
   const size_t c_bytes = 8 * W * (size_t)((n - 1) * ld + N);
   const bool hC = !on_device(C), hOcc = !on_device(occ), hOut = !on_device(out);
@@ -1179,7 +1180,11 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
     base += align_up(8 * (size_t)count);
   }
   if (hOut) dOut = reinterpret_cast<double*>(base);
-  const int rc = sbp_run(h, dC, ld, (int)n, (int)N, dtype, dOcc, count, dOut, s, chunk, h->sms);
+  if (opts && (opts->arith < 0 || opts->arith > 3)) return PERM_EINVAL;
+  const bool fp64 = opts && opts->arith == PERM_ARITH_FP64;
+  if ((rc0 = ensure_ws(h, kWsDefault, s)) != PERM_OK) return rc0;
+  const int rc = sbp_run(h, dC, ld, (int)n, (int)N, dtype, dOcc, count, dOut, s, chunk, h->sms, fp64,
+                         partials_base(h));
   if (rc == 1) return PERM_ETOOBIG;
   if (rc) return PERM_ECUDA;
   if (hOut) {

@@ -162,9 +162,10 @@ cudaError_t launch_batched_fx(const BatchArgs& a, const ClassWork& c, int dtype,
 struct perm_handle_s;
 namespace perm {
 // SBP coefficients (sbp.cu): out[k] = per(C[:, occupied columns of occ[k]]); device
-// pointers; returns 0, 1 (unsupported n) or 2 (CUDA error)
+// pointers; real input on the integer pipes unless fp64; scratch: >= 33 KiB of device
+// memory for the quantised table; returns 0, 1 (unsupported n) or 2 (CUDA error)
 int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dtype, const uint64_t* docc,
-            int64_t count, double* dout, cudaStream_t stream, int chunk_log2, int sms);
+            int64_t count, double* dout, cudaStream_t stream, int chunk_log2, int sms, bool fp64, void* scratch);
 // host orchestration of perm_batched (batched_host.cu)
 int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                 int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);

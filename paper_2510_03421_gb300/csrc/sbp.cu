@@ -6,11 +6,16 @@
 //   * n <= 16: one bitstring per lane, the lane walks all 2^(n-1) Glynn terms;
 //   * n > 16: one bitstring per warp, the lanes take contiguous slices of the terms
 //     and their double-double partials are reduced by shuffles.
-// FP64 arithmetic with Kahan-compensated sums (real and complex), column sums rebuilt
-// exactly at each slice start and every 2^chunk_log2 terms (the arithmetic of the
-// batched FP64 class kernels).  A bitstring without exactly n occupied states below
-// bit N gets NaN.
+// Real input, by default: the integer-pipe arithmetic of glynn_fx.cu.  Column j of C
+// gets its own fixed-point scale 2^e_j (sum_i |c_ij| 2^e_j <= 2^61) once per call, so a
+// bitstring's scale is the sum of its columns' e_j; column sums are exact int64, the
+// product a 64-bit-mantissa software float (a few columns on the FP64 unit), the terms
+// summed in 192-bit fixed point.  Complex input (and real input with PERM_ARITH_FP64):
+// FP64 arithmetic with Kahan-compensated sums, column sums rebuilt exactly at each
+// slice start and every 2^chunk_log2 terms (the arithmetic of the batched FP64 class
+// kernels).  A bitstring without exactly n occupied states below bit N gets NaN.
 #include "device_common.cuh"
+#include "fixed_common.cuh"
 #include "internal.h"
 
 namespace perm {
@@ -171,6 +176,137 @@ __global__ void __launch_bounds__(128) sbp_kernel(SbpArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- integer pipes (real)
+// Scales and the quantised +2q table of C (n rows of N int64), one thread per column;
+// a column with a non-finite entry gets the exponent kFxBad (its bitstrings give NaN).
+__global__ void sbp_fx_prep_kernel(SbpArgs a, long long* table, int* e) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.N) return;
+  double colabs = 0.0;
+  int nonfinite = 0;
+  for (int i = 0; i < a.n; ++i) {
+    const double v = a.C[i * a.ld + j];
+    if (!isfinite(v)) nonfinite = 1;
+    colabs += fabs(v);
+  }
+  int x = 0;
+  if (colabs > 0.0) frexp(colabs, &x);
+  const int ej = 61 - x;
+  for (int i = 0; i < a.n; ++i) table[i * a.N + j] = nonfinite ? 0 : 2 * llrint(ldexp(a.C[i * a.ld + j], ej));
+  e[j] = nonfinite ? kFxBad : ej;
+}
+
+// Unnormalised Glynn terms [g, g + len) of sC[:, col[0..n)] into a 192-bit accumulator
+// (columns j >= n are the constant 2^31, counted in es).
+template <int NP, int K>
+__device__ __forceinline__ void sbp_fx_slice(const long long* __restrict__ sq, int N, int n, const int (&col)[NP],
+                                             int es, uint64_t g, uint64_t len, u64 (&acc)[3], int& e_lo) {
+  long long S[NP];
+  bool anchored = false;
+  e_lo = 0;
+  acc[0] = acc[1] = acc[2] = 0;
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) S[j] = 0;
+      for (int i = 0; i < n; ++i) {
+        const bool minus = (gray >> (n - 1 - i)) & 1u;
+        const long long* row = sq + i * N;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          if (j < n) S[j] += minus ? -row[col[j]] : row[col[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < NP; ++j) S[j] = (j < n) ? (S[j] >> 1) : (1ll << 31);
+    } else {
+      const int b = ctz64(g);
+      const bool plus = (g >> (b + 1)) & 1u;
+      const long long* row = sq + (n - 1 - b) * N;
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+        if (j < n) S[j] += plus ? row[col[j]] : -row[col[j]];
+    }
+    u64 P;
+    int E;
+    unsigned neg;
+    soft_product<NP, K>(S, P, E, neg);
+    if (P != 0) {
+      if (!anchored) {
+        e_lo = E - es - kAnchorBit;
+        anchored = true;
+      }
+      int p = E - 63 - es - e_lo;
+      if (p > kMaxLsb) {
+        shr192(acc[0], acc[1], acc[2], p - kMaxLsb);
+        e_lo += p - kMaxLsb;
+        p = kMaxLsb;
+      }
+      acc_add(acc[0], acc[1], acc[2], P, p, neg ^ (unsigned)(g & 1u));
+    }
+  }
+}
+
+template <int NP, int K, bool LANE>
+__global__ void __launch_bounds__(128) sbp_fx_kernel(SbpArgs a, const long long* __restrict__ table,
+                                                     const int* __restrict__ escale) {
+  extern __shared__ long long sq[];  // n x N quantised +2q
+  __shared__ int se[64];
+  const int n = a.n, N = a.N;
+  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) sq[idx] = table[idx];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) se[j] = escale[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t terms = 1ull << (n - 1);
+  for (int64_t base = LANE ? 32 * warp : warp; base < a.count; base += LANE ? 32 * warps : warps) {
+    const int64_t k = LANE ? base + lane : base;
+    if (k >= a.count) continue;
+    int col[NP];
+    bool ok = columns_of<NP>(a.occ[k], n, N, col);
+    int es = 31 * (NP - n);
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      if (j < n) {
+        if (se[col[j]] == kFxBad) ok = false;
+        es += se[col[j]];
+      }
+    uint64_t g = 0, len = terms;
+    if (!LANE) split_range(0, terms, 32, (uint64_t)lane, &g, &len);
+    dd v{0.0, 0.0};
+    if (ok) {
+      u64 acc[3];
+      int e_lo = 0;
+      sbp_fx_slice<NP, K>(sq, N, n, col, es, g, len, acc, e_lo);
+      v = to_dd(acc[0], acc[1], acc[2], e_lo);
+    }
+    if (!LANE) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = dd_add(v, shfl_down_dd(v, o));
+      if (lane != 0) continue;
+    }
+    write_coef<1>(a.out, k, v, dd{0.0, 0.0}, n, ok);
+  }
+}
+
+// FP64 columns per product, by padded order (as the square real sweep)
+constexpr int sbp_fp64_columns(int np) { return np >= 32 ? 6 : np >= 16 ? 4 : 0; }
+
+void* pick_fx(int n) {
+  switch ((n + 3) & ~3) {
+    case 4: return (void*)sbp_fx_kernel<4, 0, true>;
+    case 8: return (void*)sbp_fx_kernel<8, 0, true>;
+    case 12: return (void*)sbp_fx_kernel<12, 0, true>;
+    case 16: return (void*)sbp_fx_kernel<16, sbp_fp64_columns(16), true>;
+    case 20: return (void*)sbp_fx_kernel<20, sbp_fp64_columns(20), false>;
+    case 24: return (void*)sbp_fx_kernel<24, sbp_fp64_columns(24), false>;
+    case 28: return (void*)sbp_fx_kernel<28, sbp_fp64_columns(28), false>;
+    case 32: return (void*)sbp_fx_kernel<32, sbp_fp64_columns(32), false>;
+    default: return nullptr;
+  }
+}
+
 template <int W>
 void* pick_w(int n) {
   switch ((n + 3) & ~3) {
@@ -189,12 +325,13 @@ void* pick_w(int n) {
 }  // namespace
 
 int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dtype, const uint64_t* docc,
-            int64_t count, double* dout, cudaStream_t stream, int chunk_log2, int sms) {
-  const int W = dtype == 1 ? 2 : 1;
-  void* k = W == 2 ? pick_w<2>(n) : pick_w<1>(n);
-  if (!k) return 1;
+            int64_t count, double* dout, cudaStream_t stream, int chunk_log2, int sms, bool fp64, void* scratch) {
   (void)h;
-  const size_t smem = (size_t)W * n * N * sizeof(double);
+  const int W = dtype == 1 ? 2 : 1;
+  const bool integer = W == 1 && !fp64;
+  void* k = integer ? pick_fx(n) : (W == 2 ? pick_w<2>(n) : pick_w<1>(n));
+  if (!k) return 1;
+  const size_t smem = integer ? (size_t)n * N * sizeof(long long) : (size_t)W * n * N * sizeof(double);
   if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                               cudaSuccess)
     return 2;
@@ -214,6 +351,17 @@ int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dt
   a.count = count;
   a.out = dout;
   a.chunk_log2 = chunk_log2;
+  if (integer) {
+    // scratch: the n x N table and the N column exponents
+    long long* table = static_cast<long long*>(scratch);
+    int* e = reinterpret_cast<int*>(table + 64 * 64);
+    sbp_fx_prep_kernel<<<1, 64, 0, stream>>>(a, table, e);
+    if (cudaGetLastError() != cudaSuccess) return 2;
+    const long long* tp = table;
+    const int* ep = e;
+    void* params[] = {&a, &tp, &ep};
+    return cudaLaunchKernel(k, dim3((unsigned)grid), dim3(128), params, smem, stream) == cudaSuccess ? 0 : 2;
+  }
   void* params[] = {&a};
   return cudaLaunchKernel(k, dim3((unsigned)grid), dim3(128), params, smem, stream) == cudaSuccess ? 0 : 2;
 }

@@ -100,3 +100,26 @@ def test_host_buffers_bad_bitstrings_and_errors(capi, dev):
     with pytest.raises(capi.PermError) as e:
         capi.perm_sbp(np.ones((3, 5), dtype=np.uint8), occ)
     assert e.value.status == capi.PERM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("arith", [1, 2, 3])
+def test_real_arithmetics_and_nonfinite_columns(capi, dev, arith):
+    # real input: integer pipes by default (FIXED, MIXED), FP64 sweep with arith = FP64;
+    # a non-finite entry spoils exactly the coefficients whose bitstrings occupy its column
+    import torch
+    g = inputs.rng(9940 + arith)
+    for n, N in ((9, 15), (14, 20), (18, 22)):
+        C = g.uniform(-1, 1, (n, N))
+        C[2, 5] = np.nan
+        occ = sample_occ(g, n, N, 64)
+        out = capi.perm_sbp(torch.from_numpy(C).to(dev), torch.from_numpy(occ.view(np.int64)).to(dev),
+                            opts=dict(arith=arith))
+        torch.cuda.synchronize(dev)
+        got = out.cpu().numpy()
+        for k in range(0, len(occ), 5 if n < 18 else 16):
+            cols = [j for j in range(N) if (int(occ[k]) >> j) & 1]
+            if 5 in cols:
+                assert np.isnan(got[k])
+            else:  # (the oracle's product C P would carry NaN * 0 = NaN from column 5)
+                clean = np.nan_to_num(C)
+                close(got[k], oracle.sbp_coefficient(clean, int(occ[k]), "ld" if n < 14 else "f64"), C[:, cols])
