@@ -91,13 +91,15 @@ __device__ __forceinline__ void sbp_slice(const double* __restrict__ sC, int N, 
 }
 
 // Column list of bitstring m; false unless exactly n bits are set, all below bit N.
+// Every entry of col is a valid column index (0 for a rejected bitstring).
 template <int NP>
 __device__ __forceinline__ bool columns_of(uint64_t m, int n, int N, int (&col)[NP]) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) col[j] = 0;
   const uint64_t below = (N >= 64) ? ~0ull : ((1ull << N) - 1);
   if ((m & ~below) != 0 || __popcll(m) != n) return false;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    col[j] = 0;
     if (j < n) {
       col[j] = __ffsll((long long)m) - 1;
       m &= m - 1;
@@ -266,12 +268,14 @@ __global__ void __launch_bounds__(128) sbp_fx_kernel(SbpArgs a, const long long*
     int col[NP];
     bool ok = columns_of<NP>(a.occ[k], n, N, col);
     int es = 31 * (NP - n);
+    if (ok) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j)
-      if (j < n) {
-        if (se[col[j]] == kFxBad) ok = false;
-        es += se[col[j]];
-      }
+      for (int j = 0; j < NP; ++j)
+        if (j < n) {
+          if (se[col[j]] == kFxBad) ok = false;
+          es += se[col[j]];
+        }
+    }
     uint64_t g = 0, len = terms;
     if (!LANE) split_range(0, terms, 32, (uint64_t)lane, &g, &len);
     dd v{0.0, 0.0};
