@@ -69,6 +69,9 @@ def _load():
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
             lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
             lib.oracle_glynn_partial_i128.argtypes = [i, i, p, i64, u64, u64, p]
+            for name in ("oracle_definition_ci128", "oracle_glynn_ci128"):
+                getattr(lib, name).argtypes = [i, i, p, i64, p]
+            lib.oracle_glynn_partial_ci128.argtypes = [i, i, p, i64, u64, u64, p]
             lib.oracle_subset_dp_i128.argtypes = [i, i, p, i64, p]
             lib.oracle_subset_dp_i128.restype = i
             lib.oracle_glynn_flips.argtypes = [i, p, i64]
@@ -300,3 +303,43 @@ def sbp_coefficient(C, occ: int, prec: str = "ld"):
     P = sbp_selection_matrix(int(occ), N, n)
     M = C @ P.astype(C.dtype)
     return glynn(M, prec)
+
+
+def _gaussian(re, im):
+    re = np.asarray(re, dtype=np.int64)
+    im = np.asarray(im, dtype=np.int64)
+    if re.shape != im.shape or re.ndim != 2:
+        raise ValueError("real and imaginary parts must be equal-shaped matrices")
+    if re.shape[0] > re.shape[1]:
+        re, im = re.T, im.T
+    A = np.ascontiguousarray(np.stack([re, im], axis=-1))
+    return A, A.shape[0], A.shape[1]
+
+
+def _call_gaussian(name, re, im, extra=()):
+    lib = _load()
+    A, m, n = _gaussian(re, im)
+    if m == 0:
+        return (1, 0)
+    if n > MAX_N:
+        raise ValueError("the oracle handles n <= %d" % MAX_N)
+    out = (ctypes.c_uint64 * 4)()
+    getattr(lib, name)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, *extra, out)
+    return (_i128(out[0:2]), _i128(out[2:4]))
+
+
+def definition_gaussian(re, im):
+    """Permanent of the Gaussian-integer matrix re + i im by the definition (Eq.
+    rectangular_permanent_definition), exact in wrapping 128-bit integers: (re, im)."""
+    return _call_gaussian("oracle_definition_ci128", re, im)
+
+
+def glynn_gaussian(re, im):
+    """Glynn (Eq. glynn_rectangle; the appendix algorithms) for the Gaussian-integer
+    matrix re + i im, exact in wrapping 128-bit integers: (re, im) Python ints."""
+    return _call_gaussian("oracle_glynn_ci128", re, im)
+
+
+def glynn_partial_gaussian(re, im, g0: int, g1: int):
+    """Unnormalised Glynn sum over terms g0 <= g < g1 of re + i im, modulo 2^128 (signed)."""
+    return _call_gaussian("oracle_glynn_partial_ci128", re, im, extra=(g0, g1))

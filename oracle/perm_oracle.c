@@ -168,6 +168,111 @@ void oracle_glynn_i128(int m, int n, const int64_t* A, int64_t ld, uint64_t* out
   put_i128((u128)(v / norm), out);
 }
 
+/* ---------------------------------------------------------------------------
+ * Gaussian integers (complex entries with int64 real and imaginary parts, stored
+ * as interleaved pairs, ld counted in complex elements): the same two algorithms
+ * with every product and sum taken componentwise in wrapping 128-bit integers.
+ * Output: out[0..1] = real part, out[2..3] = imaginary part (low, high words).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  u128 re, im;
+} ci128;
+
+static ci128 ci_mul(ci128 a, ci128 b) {
+  ci128 r;
+  r.re = a.re * b.re - a.im * b.im;
+  r.im = a.re * b.im + a.im * b.re;
+  return r;
+}
+
+static void def_rec_ci(int m, int n, const int64_t* A, int64_t ld, int i, int* sigma, int* used, ci128* acc) {
+  if (i == m) {
+    ci128 p = {1, 0};
+    for (int r = 0; r < m; ++r) {
+      const int64_t* e = A + 2 * (r * ld + sigma[r]);
+      ci128 a = {(u128)(i128)e[0], (u128)(i128)e[1]};
+      p = ci_mul(p, a);
+    }
+    acc->re += p.re;
+    acc->im += p.im;
+    return;
+  }
+  for (int j = 0; j < n; ++j) {
+    if (used[j]) continue;
+    used[j] = 1;
+    sigma[i] = j;
+    def_rec_ci(m, n, A, ld, i + 1, sigma, used, acc);
+    used[j] = 0;
+  }
+}
+
+void oracle_definition_ci128(int m, int n, const int64_t* A, int64_t ld, uint64_t* out) {
+  int sigma[64], used[64] = {0};
+  ci128 acc = {0, 0};
+  def_rec_ci(m, n, A, ld, 0, sigma, used, &acc);
+  put_i128(acc.re, out);
+  put_i128(acc.im, out + 2);
+}
+
+static ci128 glynn_term_ci(int m, int n, const int64_t* A, int64_t ld, const int* delta) {
+  ci128 prod = {1, 0};
+  for (int j = 0; j < n; ++j) {
+    i128 sr = 0, si = 0;
+    for (int i = 0; i < m; ++i) {
+      sr += (i128)A[2 * (i * ld + j)] * delta[i];
+      si += (i128)A[2 * (i * ld + j) + 1] * delta[i];
+    }
+    for (int k = m; k < n; ++k) sr += delta[k];
+    ci128 s = {(u128)sr, (u128)si};
+    prod = ci_mul(prod, s);
+  }
+  return prod;
+}
+
+void oracle_glynn_ci128(int m, int n, const int64_t* A, int64_t ld, uint64_t* out) {
+  int delta[64] = {0}, perm[64] = {0};
+  for (int i = 0; i < n; ++i) { delta[i] = 1; perm[i] = i; }
+  ci128 acc = glynn_term_ci(m, n, A, ld, delta);
+  int bound = n - 1, pos = 0, sign = 1;
+  while (pos != bound) {
+    sign = -sign;
+    delta[bound - pos] = -delta[bound - pos];
+    ci128 t = glynn_term_ci(m, n, A, ld, delta);
+    if (sign < 0) {
+      acc.re -= t.re;
+      acc.im -= t.im;
+    } else {
+      acc.re += t.re;
+      acc.im += t.im;
+    }
+    pos = focus_pointer_next(perm, pos);
+  }
+  i128 norm = (i128)1 << bound;
+  for (int i = 2; i <= n - m; ++i) norm *= i;
+  put_i128((u128)((i128)acc.re / norm), out);
+  put_i128((u128)((i128)acc.im / norm), out + 2);
+}
+
+void oracle_glynn_partial_ci128(int m, int n, const int64_t* A, int64_t ld, uint64_t g0, uint64_t g1,
+                                uint64_t* out) {
+  int delta[64] = {0};
+  ci128 acc = {0, 0};
+  for (uint64_t g = g0; g < g1; ++g) {
+    uint64_t gray = g ^ (g >> 1);
+    for (int i = 0; i < n; ++i) delta[i] = ((gray >> (n - 1 - i)) & 1u) ? -1 : 1;
+    ci128 t = glynn_term_ci(m, n, A, ld, delta);
+    if (g & 1u) {
+      acc.re -= t.re;
+      acc.im -= t.im;
+    } else {
+      acc.re += t.re;
+      acc.im += t.im;
+    }
+  }
+  put_i128(acc.re, out);
+  put_i128(acc.im, out + 2);
+}
+
 /* Unnormalised Glynn partial sum over terms g0 <= g < g1 (same term indexing as
  * oracle_glynn_partial_ld), modulo 2^128. */
 void oracle_glynn_partial_i128(int m, int n, const int64_t* A, int64_t ld, uint64_t g0, uint64_t g1, uint64_t* out) {

@@ -437,3 +437,43 @@ def test_sbp_selection_matrix_and_closed_forms():
     occ = 0b1001010010
     expect = math.factorial(4) * float(np.prod(u)) * float(np.prod([v[j] for j in range(10) if (occ >> j) & 1]))
     assert _rel(oracle.sbp_coefficient(np.outer(u, v), occ), expect) < 1e-13
+
+
+# ------------------------------------------------ Gaussian integers (exact, 128-bit)
+def _gaussian_brute(re, im):
+    """Exact permanent of re + i im by enumerating the m-permutations, in Python ints."""
+    m, n = re.shape
+    sr = si = 0
+    for perm in itertools.permutations(range(n), m):
+        pr, pi = 1, 0
+        for r, c in enumerate(perm):
+            a, b = int(re[r, c]), int(im[r, c])
+            pr, pi = pr * a - pi * b, pr * b + pi * a
+        sr += pr
+        si += pi
+    return sr, si
+
+
+@pytest.mark.parametrize("m,n", [(1, 3), (3, 3), (3, 5), (4, 6), (5, 5), (2, 7)])
+def test_gaussian_glynn_and_definition_equal_brute_force(m, n):
+    g = inputs.rng(220 + 10 * m + n)
+    re, im = g.integers(-4, 5, (m, n)), g.integers(-4, 5, (m, n))
+    sr, si = _gaussian_brute(re, im)
+    assert oracle.definition_gaussian(re, im) == (sr, si)
+    assert oracle.glynn_gaussian(re, im) == (sr, si)
+    assert oracle.glynn_gaussian(re.T, im.T) == (sr, si)  # transpose rule
+
+
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_gaussian_closed_forms(n):
+    # real-valued input: the real integer permanent; purely imaginary input:
+    # per(i A) = i^n per(A); all entries 1 + i: (1 + i)^n n!
+    g = inputs.rng(230 + n)
+    A = g.integers(-5, 6, (n, n))
+    p = oracle.glynn(A)
+    Z = np.zeros_like(A)
+    assert oracle.glynn_gaussian(A, Z) == (p, 0)
+    ipow = [(1, 0), (0, 1), (-1, 0), (0, -1)][n % 4]
+    assert oracle.glynn_gaussian(Z, A) == (ipow[0] * p, ipow[1] * p)
+    w = (1 + 1j) ** n * math.factorial(n)
+    assert oracle.glynn_gaussian(np.ones((n, n), int), np.ones((n, n), int)) == (int(w.real), int(w.imag))
