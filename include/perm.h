@@ -46,7 +46,10 @@ typedef enum {
   PERM_F64 = 0,  /* double */
   PERM_C128 = 1, /* complex double, interleaved (re, im) */
   PERM_U8 = 2,   /* uint8 entries (0/1 biadjacency matrices), exact integer result */
-  PERM_I64 = 3   /* int64 entries, exact integer result */
+  PERM_I64 = 3,  /* int64 entries, exact integer result */
+  PERM_CI64 = 4  /* Gaussian integers: interleaved (re, im) int64 pairs, exact result as two
+                    int128 (real part, then imaginary part; 32 bytes); perm_glynn and
+                    perm_glynn_partial only, n <= 32 */
 } perm_dtype;
 
 typedef enum {

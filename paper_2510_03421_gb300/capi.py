@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libperm.so")
 
-PERM_F64, PERM_C128, PERM_U8, PERM_I64 = 0, 1, 2, 3
+PERM_F64, PERM_C128, PERM_U8, PERM_I64, PERM_CI64 = 0, 1, 2, 3, 4
 PERM_OK, PERM_EINVAL, PERM_ETOOBIG, PERM_EOVERFLOW, PERM_ECUDA, PERM_ENOMEM, PERM_EUNSUPPORTED = range(7)
 PERM_ARITH_AUTO, PERM_ARITH_FP64, PERM_ARITH_FIXED, PERM_ARITH_MIXED = 0, 1, 2, 3
 PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
@@ -282,6 +282,50 @@ def perm_sbp(C, occ, out=None, stream=None, opts=None):
     return out
 
 
+def _gaussian(re, im):
+    """(keepalive, pointer, m, n, ld, device) of the Gaussian-integer matrix re + i im as
+    interleaved int64 pairs."""
+    if _is_torch(re):
+        import torch
+        G = torch.stack([re.to(torch.int64), im.to(torch.int64)], dim=-1).contiguous()
+        m, n = G.shape[0], G.shape[1]
+        return G, G.data_ptr(), m, n, n, (G.device if G.is_cuda else None)
+    G = np.ascontiguousarray(np.stack([np.asarray(re, np.int64), np.asarray(im, np.int64)], axis=-1))
+    return G, G.ctypes.data, G.shape[0], G.shape[1], G.shape[1], None
+
+
+def _gaussian_out(dev):
+    if dev is not None:
+        import torch
+        return torch.zeros(4, dtype=torch.int64, device=dev)
+    return np.zeros(4, dtype=np.int64)
+
+
+def perm_glynn_gaussian(re, im, out=None, stream=None, opts=None):
+    """Exact permanent of the Gaussian-integer matrix re + i im (int64 parts): out holds
+    two int128 (real, imaginary); read it with value(out, PERM_CI64)."""
+    keep, p, m, n, ld, dev = _gaussian(re, im)
+    if out is None:
+        out = _gaussian_out(dev)
+    rc = lib().perm_glynn(handle(_device_index(dev)), p, m, n, ld, PERM_CI64, _ptr(out), _stream(dev, stream),
+                          _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_glynn")
+    return out
+
+
+def perm_glynn_partial_gaussian(re, im, g_begin: int, g_end: int, out=None, stream=None, opts=None):
+    """Unnormalised Glynn sum of re + i im over terms [g_begin, g_end), modulo 2^128."""
+    keep, p, m, n, ld, dev = _gaussian(re, im)
+    if out is None:
+        out = _gaussian_out(dev)
+    rc = lib().perm_glynn_partial(handle(_device_index(dev)), p, m, n, ld, PERM_CI64, g_begin, g_end, _ptr(out),
+                                  _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_glynn_partial")
+    return out
+
+
 def perm_glynn_noalloc(A, out=None, stream=None, grid: int = 0):
     """Real Glynn sweep that allocates nothing (scratch is a fixed device array in the
     library); A and out must be CUDA tensors on the current device."""
@@ -377,11 +421,20 @@ def perm_probe_rate(kind: int, device: int = 0, stream=None) -> float:
 
 
 # ----------------------------------------------------------------------------- results
+def _int128(lo, hi) -> int:
+    v = (int(lo) & (2 ** 64 - 1)) | ((int(hi) & (2 ** 64 - 1)) << 64)
+    return v - (1 << 128) if v >> 127 else v
+
+
 def value(out, code: int, index: int = 0):
-    """Python value of result `index` of `out` (float, complex or exact int)."""
+    """Python value of result `index` of `out` (float, complex, exact int, or a
+    (real, imaginary) pair of exact ints for Gaussian integers)."""
     arr = out.detach().cpu().numpy() if _is_torch(out) else np.asarray(out)
     if code == PERM_F64:
         return float(arr.reshape(-1)[index])
+    if code == PERM_CI64:
+        q = arr.reshape(-1, 4)[index]
+        return (_int128(q[0], q[1]), _int128(q[2], q[3]))
     row = arr.reshape(-1, 2)[index]
     if code == PERM_C128:
         return complex(float(row[0]), float(row[1]))

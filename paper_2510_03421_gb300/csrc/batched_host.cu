@@ -369,8 +369,8 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
                 int64_t count, int dtype, void* out, cudaStream_t s, const void* opts_v) {
   const perm_opts* opts = static_cast<const perm_opts*>(opts_v);
   if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
-  if (dtype != PERM_F64 && dtype != PERM_C128) return (dtype == PERM_U8 || dtype == PERM_I64) ? PERM_EUNSUPPORTED
-                                                                                              : PERM_EINVAL;
+  if (dtype != PERM_F64 && dtype != PERM_C128)
+    return (dtype == PERM_U8 || dtype == PERM_I64 || dtype == PERM_CI64) ? PERM_EUNSUPPORTED : PERM_EINVAL;
   if (count == 0) return PERM_OK;
   if (count > (1ll << 30)) return PERM_ETOOBIG;
   const int W = dtype == PERM_C128 ? 2 : 1;

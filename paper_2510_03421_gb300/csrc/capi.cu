@@ -28,11 +28,12 @@ size_t elem_size(int dtype) {
     case PERM_C128: return 16;
     case PERM_U8: return 1;
     case PERM_I64: return 8;
+    case PERM_CI64: return 16;
     default: return 0;
   }
 }
 
-size_t out_size(int dtype) { return dtype == PERM_F64 ? 8 : 16; }
+size_t out_size(int dtype) { return dtype == PERM_F64 ? 8 : dtype == PERM_CI64 ? 32 : 16; }
 
 bool on_device(const void* p) {
   cudaPointerAttributes at;
@@ -154,7 +155,7 @@ int finish(Call& c, size_t out_bytes) {
     if (c.hErr && cudaMemcpyAsync(c.hErr, c.dErr, sizeof(double), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
       return PERM_ECUDA;
     int dev_status = 0;
-    if (c.dtype == PERM_U8 || c.dtype == PERM_I64) {
+    if (c.dtype == PERM_U8 || c.dtype == PERM_I64 || c.dtype == PERM_CI64) {
       // host result: the integer range check is reported synchronously
       int* sw = reinterpret_cast<int*>(static_cast<char*>(c.h->ws) + kStageA + 132);
       if (cudaMemcpyAsync(&dev_status, sw, sizeof(int), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess)
@@ -416,6 +417,29 @@ int glynn_integer(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
   if (launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
                         static_cast<unsigned long long*>(c.dOut), raw, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
+// Glynn for Gaussian integers, exact modulo 2^128 per component (glynn_int.cu).
+int glynn_gaussian(Call& c, bool raw, uint64_t g0, uint64_t g1) {
+  if (c.n > glynn_gaussian_max_n()) return PERM_ETOOBIG;
+  const int block = 128;
+  if (c.o.block > block) return PERM_EINVAL;
+  int bps = glynn_gaussian_blocks_per_sm(c.n, c.o.block ? c.o.block : block);
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, 2 * kIntRecord * sizeof(unsigned long long));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, g0, g1, 62);
+  int* st = c.hOut ? call_status_word(c.h) : status_word(c.h);
+  if (c.hOut && cudaMemsetAsync(st, 0, sizeof(int), c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (!raw && launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, st, c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (launch_glynn_gaussian(a, lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream) != cudaSuccess) return PERM_ECUDA;
+  const unsigned long long* rec = static_cast<const unsigned long long*>(a.partials);
+  unsigned long long* out = static_cast<unsigned long long*>(c.dOut);
+  if (launch_finish_int(rec, lc.grid, c.n - 1, c.n - c.m, out, raw, c.stream) != cudaSuccess ||
+      launch_finish_int(rec + kIntRecord * lc.grid, lc.grid, c.n - 1, c.n - c.m, out + 2, raw, c.stream) !=
+          cudaSuccess)
     return PERM_ECUDA;
   return PERM_OK;
 }
@@ -901,6 +925,7 @@ int perm_glynn(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
   switch (dtype) {
     case PERM_F64: rc = glynn_real(c, false, 0, terms); break;
     case PERM_C128: rc = glynn_cplx(c, false, 0, terms); break;
+    case PERM_CI64: rc = glynn_gaussian(c, false, 0, terms); break;
     default: rc = glynn_integer(c, false, 0, terms); break;
   }
   if (rc) return rc;
@@ -924,6 +949,10 @@ int perm_glynn_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64
       break;
     case PERM_C128:
       rc = glynn_cplx(c, true, g_begin, g_end);
+      bytes = 32;
+      break;
+    case PERM_CI64:
+      rc = glynn_gaussian(c, true, g_begin, g_end);
       bytes = 32;
       break;
     default:
@@ -952,6 +981,7 @@ int perm_ryser_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64
 int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
                const perm_opts* opts) {
   Call c;
+  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {
@@ -970,6 +1000,7 @@ int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
 int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
                       void* stream, const perm_opts* opts) {
   Call c;
+  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {
@@ -985,6 +1016,7 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
               const perm_opts* opts) {
   Call c;
+  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {
@@ -1113,6 +1145,7 @@ int perm_auto_choice(perm_handle h, const void* A, int64_t m, int64_t n, int64_t
                      int* candidate, float* predicted) {
   if (!candidate) return PERM_EINVAL;
   Call c;
+  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;
   double dummy_out[2];
   int rc = prepare(c, h, A, m, n, ld, dtype, dummy_out, nullptr, opts, true);
   if (rc) return rc;
@@ -1136,7 +1169,7 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
 int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,
              int64_t count, void* out, void* stream, const perm_opts* opts) {
   if (!h) return PERM_EINVAL;
-  if (dtype == PERM_U8 || dtype == PERM_I64) return PERM_EUNSUPPORTED;
+  if (dtype == PERM_U8 || dtype == PERM_I64 || dtype == PERM_CI64) return PERM_EUNSUPPORTED;
   if (dtype != PERM_F64 && dtype != PERM_C128) return PERM_EINVAL;
   if (count < 0 || n < 1 || N < n || ld < N) return PERM_EINVAL;
   if (count > 0 && (!C || !occ || !out)) return PERM_EINVAL;

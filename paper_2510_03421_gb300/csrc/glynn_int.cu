@@ -210,6 +210,133 @@ void* pick_grouped(int n, int dtype) {
   }
 }
 
+// Gaussian integers (dtype 4): the same walk with complex column sums (int64 real and
+// imaginary parts) and complex products and sums modulo 2^128 per component.  The
+// per-block records are written as two arrays of int128: the real parts at records
+// [0, grid), the imaginary parts at [grid, 2 grid).
+template <int N>
+__global__ void __launch_bounds__(128) glynn_cint_kernel(SweepArgs a) {
+  extern __shared__ long long smem_i[];
+  __shared__ u128 scratch[2 * 32];
+  const int n = a.n, m = a.m;
+  long long* sP = smem_i;              // +2 a'_ij as (re, im) at 2 (i N + j)
+  long long* sM = smem_i + 2 * n * N;  // -2 a'_ij
+  const long long* A = static_cast<const long long*>(a.A);
+  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    long long vr = 0, vi = 0;
+    if (j < n) {
+      if (i < m) {
+        vr = A[2 * (i * a.rs + j * a.cs)];
+        vi = A[2 * (i * a.rs + j * a.cs) + 1];
+      } else {
+        vr = 1;
+      }
+    }
+    sP[2 * idx] = 2 * vr;
+    sP[2 * idx + 1] = 2 * vi;
+    sM[2 * idx] = -2 * vr;
+    sM[2 * idx + 1] = -2 * vi;
+  }
+  __syncthreads();
+
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t g, len;
+  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+
+  u128 acc_r = 0, acc_i = 0;
+  long long Sr[N], Si[N];
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Sr[j] = 0;
+        Si[j] = 0;
+      }
+      for (int i = 0; i < n; ++i) {
+        const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + 2 * i * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          Sr[j] += row[2 * j];
+          Si[j] += row[2 * j + 1];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Sr[j] = (j < n) ? Sr[j] / 2 : 1;
+        Si[j] = (j < n) ? Si[j] / 2 : 0;
+      }
+    } else {
+      const int b = ctz64(g);
+      const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + 2 * (n - 1 - b) * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Sr[j] += row[2 * j];
+        Si[j] += row[2 * j + 1];
+      }
+    }
+    u128 pr = (u128)(__int128)Sr[0], pi = (u128)(__int128)Si[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) {
+      const u128 nr = mul_s64(pr, Sr[j]) - mul_s64(pi, Si[j]);
+      const u128 ni = mul_s64(pr, Si[j]) + mul_s64(pi, Sr[j]);
+      pr = nr;
+      pi = ni;
+    }
+    if (g & 1u) {
+      acc_r -= pr;
+      acc_i -= pi;
+    } else {
+      acc_r += pr;
+      acc_i += pi;
+    }
+  }
+
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc_r += shfl_down_u128(acc_r, off);
+    acc_i += shfl_down_u128(acc_i, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    scratch[warp] = acc_r;
+    scratch[32 + warp] = acc_i;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    u128 xr = (lane < nw) ? scratch[lane] : (u128)0;
+    u128 xi = (lane < nw) ? scratch[32 + lane] : (u128)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      xr += shfl_down_u128(xr, off);
+      xi += shfl_down_u128(xi, off);
+    }
+    if (lane == 0) {
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials);
+      rec[kIntRecord * blockIdx.x] = (unsigned long long)xr;
+      rec[kIntRecord * blockIdx.x + 1] = (unsigned long long)(xr >> 64);
+      rec[kIntRecord * (gridDim.x + blockIdx.x)] = (unsigned long long)xi;
+      rec[kIntRecord * (gridDim.x + blockIdx.x) + 1] = (unsigned long long)(xi >> 64);
+    }
+  }
+}
+
+void* pick_gaussian(int n) {
+  switch ((n + 3) & ~3) {
+    case 4: return (void*)glynn_cint_kernel<4>;
+    case 8: return (void*)glynn_cint_kernel<8>;
+    case 12: return (void*)glynn_cint_kernel<12>;
+    case 16: return (void*)glynn_cint_kernel<16>;
+    case 20: return (void*)glynn_cint_kernel<20>;
+    case 24: return (void*)glynn_cint_kernel<24>;
+    case 28: return (void*)glynn_cint_kernel<28>;
+    case 32: return (void*)glynn_cint_kernel<32>;
+    default: return nullptr;
+  }
+}
+
 template <int N>
 void* kernel_for(int dtype) {
   return dtype == 2 ? (void*)glynn_int_kernel<N, unsigned char> : (void*)glynn_int_kernel<N, long long>;
@@ -243,6 +370,14 @@ size_t smem_bytes(int n) { return 2u * (size_t)n * (size_t)((n + 3) & ~3) * size
 // and, for 0/1 matrices, of 2^(n-1) times Bregman's bound prod_i (r_i!)^(1/r_i) on
 // the permanent of the padded matrix A' (pad rows have n ones).  Also guards the
 // int64 column sums.  Sets *status = PERM_EOVERFLOW (3) if exactness is not assured.
+// |a| of element e (Gaussian integers: |re| + |im|, an upper bound of the modulus).
+__device__ __forceinline__ double mag_of(const void* A, int dtype, int64_t e) {
+  if (dtype == 2) return (double)static_cast<const unsigned char*>(A)[e];
+  const long long* p = static_cast<const long long*>(A);
+  if (dtype == 4) return fabs((double)p[2 * e]) + fabs((double)p[2 * e + 1]);
+  return fabs((double)p[e]);
+}
+
 __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double ln2 = 0.69314718055994530942;
@@ -252,9 +387,8 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
     double rsum = 0.0;
     for (int j = 0; j < n; ++j) {
       const int64_t e = i * rs + j * cs;
-      double v = dtype == 2 ? (double)static_cast<const unsigned char*>(A)[e]
-                            : fabs((double)static_cast<const long long*>(A)[e]);
-      if (v > 1.0) binary = false;
+      const double v = mag_of(A, dtype, e);
+      if (v > 1.0 || dtype == 4) binary = false;
       rsum += v;
     }
     if (rsum == 0.0) zero_row = true;
@@ -267,8 +401,7 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
     double csum = 0.0;
     for (int i = 0; i < m; ++i) {
       const int64_t e = i * rs + j * cs;
-      csum += dtype == 2 ? (double)static_cast<const unsigned char*>(A)[e]
-                         : fabs((double)static_cast<const long long*>(A)[e]);
+      csum += mag_of(A, dtype, e);
     }
     if (csum + (double)(n - m) > 2.0e18) col_overflow = true;  // 2 * 2^62 headroom for the +-2 a updates
   }
@@ -307,6 +440,26 @@ cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c, 
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  SweepArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
+}
+
+int glynn_gaussian_max_n() { return 32; }
+
+int glynn_gaussian_blocks_per_sm(int n, int block) {
+  void* k = pick_gaussian(n);
+  if (!k) return 0;
+  const size_t smem = 4u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_glynn_gaussian(const SweepArgs& a, const LaunchCfg& c) {
+  void* k = pick_gaussian(a.n);
+  if (!k) return cudaErrorInvalidValue;
+  const size_t smem = 4u * (size_t)a.n * (size_t)((a.n + 3) & ~3) * sizeof(long long);  // <= 32 KiB
   SweepArgs args = a;
   void* params[] = {&args};
   return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);

@@ -84,6 +84,11 @@ int glynn_c128_max_n();
 // grouped: the rectangular walk over the 2^(m-1) real-row sign vectors (1 <= m < n)
 cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c, bool grouped);
 int glynn_int_blocks_per_sm(int n, int dtype, int block, bool grouped);
+// Gaussian integers (dtype 4, n <= glynn_gaussian_max_n()): records as two int128 arrays
+// (real parts at [0, grid), imaginary parts at [grid, 2 grid))
+cudaError_t launch_glynn_gaussian(const SweepArgs& a, const LaunchCfg& c);
+int glynn_gaussian_blocks_per_sm(int n, int block);
+int glynn_gaussian_max_n();
 // a-priori int128 range check; writes 3 (PERM_EOVERFLOW) to *status if exactness is not assured
 cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
                              cudaStream_t s);

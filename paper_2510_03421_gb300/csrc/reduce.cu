@@ -103,6 +103,10 @@ __global__ void write_one_kernel(int dtype, void* out) {
   } else {
     static_cast<unsigned long long*>(out)[0] = 1ull;
     static_cast<unsigned long long*>(out)[1] = 0ull;
+    if (dtype == 4) {  // Gaussian integers: imaginary part 0
+      static_cast<unsigned long long*>(out)[2] = 0ull;
+      static_cast<unsigned long long*>(out)[3] = 0ull;
+    }
   }
 }
 
