@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import device, to_dev
+from gpu_util import close, device, to_dev
 from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -78,3 +78,24 @@ def test_limits_and_empty(capi, dev):
         out = getattr(capi, fn)(torch.zeros((0, 5), dtype=torch.float64, device=dev))
         torch.cuda.synchronize(dev)
         assert capi.value(out, capi.PERM_F64) == 1.0, fn
+
+
+def test_leading_dimension_larger_than_n(capi, dev):
+    # a column slice of a wider matrix: rows ld = 24 elements apart, read through the strides
+    import torch
+    g = inputs.rng(8110)
+    for big, ref_of in ((g.uniform(-1, 1, (18, 24)), oracle.glynn),
+                        (g.uniform(-1, 1, (11, 24)) + 1j * g.uniform(-1, 1, (11, 24)), oracle.glynn),
+                        (g.integers(-3, 4, (12, 24)).astype(np.int64), oracle.subset_dp)):
+        T = torch.from_numpy(big).to(dev)
+        view = T[:, :17] if big.shape[0] <= 17 else T[:, :18]
+        assert view.stride(0) == 24
+        A = big[:, :view.shape[1]]
+        out = capi.perm_glynn(view)
+        torch.cuda.synchronize(dev)
+        got = capi.value(out, capi.dtype_code(view))
+        ref = ref_of(np.ascontiguousarray(A))
+        if big.dtype == np.int64:
+            assert got == ref
+        else:
+            close(got, ref, A, rel=1e-12)
