@@ -5,7 +5,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 (``paper_2510_03421_gb300``) and the library never imports it.
 
 The arithmetic lives in ``perm_oracle.c`` (plain serial C, compiled with gcc by
-:func:`build`); this module only marshals numpy arrays into it.
+:func:`build`); this module only marshals numpy arrays into it.  The exception is
+:mod:`oracle.cauchy`: permanents of Cauchy matrices in exact rationals
+(``fractions.Fraction``), by the definition and by Borchardt's theorem.
 
 Conventions (the paper's rectangular definition, Eq. rectangular_permanent_definition):
 
@@ -343,3 +345,7 @@ def glynn_gaussian(re, im):
 def glynn_partial_gaussian(re, im, g0: int, g1: int):
     """Unnormalised Glynn sum over terms g0 <= g < g1 of re + i im, modulo 2^128 (signed)."""
     return _call_gaussian("oracle_glynn_partial_ci128", re, im, extra=(g0, g1))
+
+
+# Exact rational permanents of Cauchy matrices (Eq. caucy_permanent), pure Python.
+from . import cauchy  # noqa: E402,F401

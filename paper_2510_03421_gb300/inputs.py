@@ -93,17 +93,28 @@ def sparse01(m: int, n: int, density: float, seed: int) -> np.ndarray:
     return bernoulli01(m, n, seed, density)
 
 
-def cauchy(n: int, seed: int, draws: int = 1000) -> np.ndarray:
+def cauchy_points(n: int, seed: int, draws: int = 1, count: int = 1):
+    """Points of `count` Cauchy matrices c_ij = 1 / (x_i - y_j), the recipe of the paper's
+    accuracy tests: x ~ U[0.25, 0.75], y ~ U[-0.75, -0.25].  With draws > 1, each
+    matrix keeps the draw whose C has the smallest 2-norm condition number.  Returns
+    (x, y), each of shape (count, n)."""
     g = rng(seed)
-    best, best_cond = None, np.inf
-    for _ in range(draws):
-        x = g.uniform(0.25, 0.75, size=n)
-        y = g.uniform(-0.75, -0.25, size=n)
-        c = 1.0 / (x[:, None] - y[None, :])
-        k = np.linalg.cond(c)
-        if k < best_cond:
-            best, best_cond = c, k
-    return best
+    xs = np.empty((count, n))
+    ys = np.empty((count, n))
+    for b in range(count):
+        best_cond = np.inf
+        for _ in range(draws):
+            x = g.uniform(0.25, 0.75, size=n)
+            y = g.uniform(-0.75, -0.25, size=n)
+            k = np.linalg.cond(1.0 / (x[:, None] - y[None, :])) if draws > 1 else 0.0
+            if k < best_cond:
+                xs[b], ys[b], best_cond = x, y, k
+    return xs, ys
+
+
+def cauchy(n: int, seed: int, draws: int = 1000) -> np.ndarray:
+    x, y = cauchy_points(n, seed, draws)
+    return 1.0 / (x[0][:, None] - y[0][None, :])
 
 
 # The five workloads, by what they are.

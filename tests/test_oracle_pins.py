@@ -477,3 +477,55 @@ def test_gaussian_closed_forms(n):
     assert oracle.glynn_gaussian(Z, A) == (ipow[0] * p, ipow[1] * p)
     w = (1 + 1j) ** n * math.factorial(n)
     assert oracle.glynn_gaussian(np.ones((n, n), int), np.ones((n, n), int)) == (int(w.real), int(w.imag))
+
+
+# --- exact Cauchy permanents (oracle.cauchy), the truth for perm_cauchy
+
+
+def test_exact_det_known_values():
+    oc = oracle.cauchy
+    # permutation matrices (every pivot search swaps rows): det = sign of the permutation
+    for perm in itertools.permutations(range(4)):
+        P = [[int(perm[i] == j) for j in range(4)] for i in range(4)]
+        inv = sum(1 for i in range(4) for j in range(i + 1, 4) if perm[i] > perm[j])
+        assert oc.det(P) == (-1) ** inv
+    # Vandermonde on integer points: prod_{i<j} (t_j - t_i)
+    t = [3, -1, 4, 10, -5, 9]
+    V = [[ti ** k for k in range(len(t))] for ti in t]
+    assert oc.det(V) == math.prod(t[j] - t[i] for i in range(len(t)) for j in range(i + 1, len(t)))
+    # singular (two equal rows) and triangular
+    assert oc.det([[1, 2, 3], [4, 5, 6], [1, 2, 3]]) == 0
+    assert oc.det([[2, 7, 1], [0, -3, 5], [0, 0, Fraction(1, 7)]]) == Fraction(-6, 7)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6, 9])
+def test_exact_det_matches_cauchy_closed_form(n):
+    # Cauchy's determinant formula is an identity independent of elimination
+    x, y = inputs.cauchy_points(n, 700 + n)
+    oc = oracle.cauchy
+    assert oc.det(oc.cauchy_matrix(x[0], y[0])) == oc.cauchy_det_closed_form(x[0], y[0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_borchardt_equals_definition_exactly(n):
+    # Eq. caucy_permanent, checked by brute force in exact rationals: the paper's point
+    # distribution, and interleaved points so that C has entries of both signs
+    oc = oracle.cauchy
+    x, y = inputs.cauchy_points(n, 710 + n)
+    C = oc.cauchy_matrix(x[0], y[0])
+    assert oc.permanent_borchardt(x[0], y[0]) == oc.permanent_definition(C)
+    g = inputs.rng(720 + n)
+    pts = g.permutation(g.uniform(-1.0, 1.0, 2 * n))
+    xi, yi = pts[:n], pts[n:]
+    C = oc.cauchy_matrix(xi, yi)
+    assert oc.permanent_borchardt(xi, yi) == oc.permanent_definition(C)
+
+
+def test_borchardt_small_closed_forms():
+    oc = oracle.cauchy
+    assert oc.permanent_borchardt([0.5], [-0.25]) == Fraction(4, 3)
+    x, y = [0.5, 0.75], [-0.25, -0.5]
+    c = [[Fraction(1) / (Fraction(a) - Fraction(b)) for b in y] for a in x]
+    assert oc.permanent_borchardt(x, y) == c[0][0] * c[1][1] + c[0][1] * c[1][0]
+    with pytest.raises(ZeroDivisionError):
+        oc.permanent_borchardt([0.5, 0.5], [-0.25, -0.5])
