@@ -157,6 +157,35 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
 int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,
              int64_t count, void* out, void* stream, const perm_opts* opts);
 
+/* Permanents of square Cauchy matrices c_ij = 1 / (x_i - y_j) by Borchardt's theorem
+ * (Eq. caucy_permanent): per(C) = det(C o C) / det(C), with det(C) from Cauchy's product
+ * formula and det(C o C) by Gaussian elimination with partial pivoting, both in a
+ * multi-limb binary floating point (up to 1024-bit mantissas, 32-bit exponents).
+ * C o C is very ill-conditioned (an elimination in double loses every digit from
+ * n ~ 12 on), so the call climbs a precision ladder: the permanent is computed at
+ * about 9 n + 96 bits and at successively longer precisions until two rungs agree to
+ * 2^-62 relative, and the longer one is returned rounded to double.  The value is the
+ * permanent of the exact Cauchy matrix of the given doubles (not of C rounded to
+ * double).
+ *   x, y     points of matrix b (0 <= b < count) at x[b n .. b n + n), y[b n .. b n + n)
+ *   n        order, 1 <= n <= 64
+ *   out      count doubles
+ *   opts     only opts->err is read: if set, count doubles receiving an error estimate
+ *            per matrix, |difference of the last two rungs| + 2^-53 |result| (an
+ *            estimate from the ladder, not a proven bound)
+ * x, y, out and opts->err may each be device or host memory; with any of them in host
+ * memory the call synchronises `stream` before returning.  A matrix with a
+ * non-finite or coinciding point (x_i = x_k, y_j = y_l or x_i = y_j, where det(C) = 0 or
+ * an entry is infinite) gets NaN and status PERM_EINVAL; one whose ladder ends without
+ * agreement (per(C) = 0 is the known case) gets NaN and PERM_ETOOBIG.  These statuses
+ * are returned by the call when out or err is in host memory, else kept for
+ * perm_device_status.  One block of 256 threads per matrix; the handle keeps about
+ * 2.6 KiB x (n^2 + n + 514) of scratch per concurrently running block.
+ * Errors: PERM_EINVAL (null pointers, n < 1, count < 0), PERM_ETOOBIG (n > 64),
+ * PERM_ENOMEM. */
+int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int64_t count, double* out,
+                void* stream, const perm_opts* opts);
+
 /* Unnormalised partial Glynn sum over the terms g_begin <= g < g_end of Eq. glynn_rectangle:
  *     sum_g (-1)^g prod_j ( sum_{i<m} delta_i(g) a_ij + sum_{i>=m} delta_i(g) ),
  * where delta_i(g) = -1 if bit (n-1-i) of gray(g) = g ^ (g >> 1) is set, else +1,
@@ -196,7 +225,8 @@ int perm_glynn_noalloc(const void* A, int64_t m, int64_t n, int64_t ld, void* ou
 /* Device-detected status since the last call of this function on handle h:
  * PERM_EOVERFLOW if an integer call whose result went to device memory could not
  * be guaranteed exact (its a-priori bound reached 2^126.5; the value written is
- * still the sum modulo 2^128), else PERM_OK.  Synchronises `stream`, then clears
+ * still the sum modulo 2^128); PERM_EINVAL or PERM_ETOOBIG if a perm_cauchy matrix
+ * got NaN (see there); else PERM_OK (one of the codes raised, if several were).  Synchronises `stream`, then clears
  * the status.  Integer calls with a host `out` report PERM_EOVERFLOW directly. */
 int perm_device_status(perm_handle h, void* stream, int* status);
 

@@ -26,7 +26,7 @@ PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
            "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status",
            "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
-           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp")
+           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp", "perm_cauchy")
 PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
 PERM_NCAND = 4
 PERM_NFEATURES = 12
@@ -67,6 +67,7 @@ def lib():
             L.perm_ryser_partial.argtypes = [vp, vp, i64, i64, i64, i32, u64, u64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_sbp.argtypes = [vp, vp, i64, i64, i64, i32, vp, i64, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_cauchy.argtypes = [vp, vp, vp, i64, i64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
             L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
             fp = ctypes.c_void_p
@@ -279,6 +280,32 @@ def perm_sbp(C, occ, out=None, stream=None, opts=None):
                         _stream(dev, stream), _opts(opts))
     if rc:
         raise PermError(rc, "perm_sbp")
+    return out
+
+
+def perm_cauchy(x, y, out=None, stream=None, opts=None):
+    """Permanents of the Cauchy matrices c_ij = 1 / (x[b, i] - y[b, j]) by Borchardt's theorem;
+    x and y are (count, n) or (n,) float64 arrays/tensors, contiguous; out gets count doubles."""
+    if _is_torch(x):
+        dev = x.device if x.is_cuda else None
+        n = x.shape[-1]
+        count = x.numel() // n if n else 0
+        if y.shape != x.shape or not x.is_contiguous() or not y.is_contiguous():
+            raise ValueError("x and y: contiguous, same shape")
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if y.shape != x.shape:
+            raise ValueError("x and y: same shape")
+        dev = None
+        n = x.shape[-1]
+        count = x.size // n if n else 0
+    if out is None:
+        out = _out_like(PERM_F64, dev, count)
+    rc = lib().perm_cauchy(handle(_device_index(dev)), _ptr(x), _ptr(y), n, count, _ptr(out),
+                           _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_cauchy")
     return out
 
 

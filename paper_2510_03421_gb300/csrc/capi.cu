@@ -834,6 +834,23 @@ uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDef
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Grow the staging / scratch buffer of perm_sbp and perm_cauchy (not during capture).
+int ensure_sws(perm_handle h, size_t need) {
+  if (need <= h->sws_bytes) return PERM_OK;
+  if (h->sws) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return PERM_ECUDA;
+    cudaFree(h->sws);
+    h->sws = nullptr;
+    h->sws_bytes = 0;
+  }
+  if (cudaMalloc(&h->sws, need) != cudaSuccess) {
+    cudaGetLastError();
+    return PERM_ENOMEM;
+  }
+  h->sws_bytes = need;
+  return PERM_OK;
+}
+
 }  // namespace
 }  // namespace perm
 
@@ -1185,19 +1202,7 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
   const bool hC = !on_device(C), hOcc = !on_device(occ), hOut = !on_device(out);
   const size_t need = (hC ? align_up(c_bytes) : 0) + (hOcc ? align_up(8 * (size_t)count) : 0) +
                       (hOut ? align_up(8 * W * (size_t)count) : 0);
-  if (need > h->sws_bytes) {
-    if (h->sws) {
-      if (cudaDeviceSynchronize() != cudaSuccess) return PERM_ECUDA;
-      cudaFree(h->sws);
-      h->sws = nullptr;
-      h->sws_bytes = 0;
-    }
-    if (cudaMalloc(&h->sws, need) != cudaSuccess) {
-      cudaGetLastError();
-      return PERM_ENOMEM;
-    }
-    h->sws_bytes = need;
-  }
+  if ((rc0 = ensure_sws(h, need)) != PERM_OK) return rc0;
   char* base = static_cast<char*>(h->sws);
   const double* dC = static_cast<const double*>(C);
   const uint64_t* dOcc = occ;
@@ -1225,6 +1230,68 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
       return PERM_ECUDA;
   }
   if (hC || hOcc || hOut) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int64_t count, double* out,
+                void* stream, const perm_opts* opts) {
+  if (!h) return PERM_EINVAL;
+  if (count < 0 || n < 1) return PERM_EINVAL;
+  if (count > 0 && (!x || !y || !out)) return PERM_EINVAL;
+  if (n > cauchy_max_n()) return PERM_ETOOBIG;
+  if (count == 0) return PERM_OK;
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* err = opts ? opts->err : nullptr;
+  const size_t pts = 8 * (size_t)(n * count);
+  const bool hx = !on_device(x), hy = !on_device(y), hOut = !on_device(out), hErr = err && !on_device(err);
+  int64_t grid = 2 * (int64_t)h->sms;
+  if (grid > count) grid = count;
+  const size_t scratch = align_up(8 * cauchy_scratch_words((int)n) * (size_t)grid);
+  const size_t need = scratch + (hx ? align_up(pts) : 0) + (hy ? align_up(pts) : 0) +
+                      (hOut ? align_up(8 * (size_t)count) : 0) + (hErr ? align_up(8 * (size_t)count) : 0);
+  int rc = ensure_sws(h, need);
+  if (rc) return rc;
+  if ((rc = ensure_ws(h, kWsDefault, s)) != PERM_OK) return rc;
+  char* base = static_cast<char*>(h->sws);
+  uint64_t* dScratch = reinterpret_cast<uint64_t*>(base);
+  base += scratch;
+  const double* dx = x;
+  const double* dy = y;
+  double* dOut = out;
+  double* dErr = err;
+  if (hx) {
+    if (cudaMemcpyAsync(base, x, pts, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dx = reinterpret_cast<const double*>(base);
+    base += align_up(pts);
+  }
+  if (hy) {
+    if (cudaMemcpyAsync(base, y, pts, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dy = reinterpret_cast<const double*>(base);
+    base += align_up(pts);
+  }
+  if (hOut) {
+    dOut = reinterpret_cast<double*>(base);
+    base += align_up(8 * (size_t)count);
+  }
+  if (hErr) dErr = reinterpret_cast<double*>(base);
+  const bool host_result = hOut || hErr;
+  int* st = host_result ? call_status_word(h) : status_word(h);
+  if (host_result && cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess) return PERM_ECUDA;
+  if (launch_cauchy(dx, dy, (int)n, count, dOut, dErr, dScratch, (int)grid, st, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (hOut && cudaMemcpyAsync(out, dOut, 8 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (hErr && cudaMemcpyAsync(err, dErr, 8 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (host_result) {
+    int dev_status = 0;
+    if (cudaMemcpyAsync(&dev_status, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PERM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+    if (dev_status) return dev_status;
+  } else if (hx || hy) {
     if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
   }
   return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;

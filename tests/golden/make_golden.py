@@ -3,7 +3,8 @@
 Every value here comes from the CPU oracle (``oracle/``) alone, on inputs drawn by
 ``paper_2510_03421_gb300.inputs``; nothing is taken from the CUDA path.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py            # all but the Cauchy values
+    python tests/golden/make_golden.py cauchy     # the Cauchy values (about 15 minutes)
 """
 import os
 import sys
@@ -79,7 +80,31 @@ def rect20x40_f64():
     ])
 
 
+def cauchy_exact():
+    # Cauchy matrices c_ij = 1 / (x_i - y_j) with the points of inputs.cauchy_points;
+    # exact rational permanents by Borchardt's theorem (oracle.cauchy), rounded to double
+    cases = [(24, 10, 1, [0]), (32, 11, 1, [0]), (40, 12, 1, [0]), (48, 13, 1, [0]), (64, 14, 1, [0]),
+             (36, 15, 1216, [0, 1, 608, 1215])]
+    lines = [
+        "# Exact permanents of Cauchy matrices c_ij = 1 / (x_i - y_j), Eq. caucy_permanent, evaluated",
+        "# in rationals by oracle.cauchy.permanent_borchardt and rounded to double.  Matrix `index` of",
+        "# inputs.cauchy_points(n, seed, count=count): x ~ U[0.25, 0.75], y ~ U[-0.75, -0.25].",
+    ]
+    for n, off, count, idx in cases:
+        seed = inputs.SEED_BASE + off
+        x, y = inputs.cauchy_points(n, seed, count=count)
+        for b in idx:
+            t0 = time.time()
+            v = oracle.cauchy.permanent_borchardt(x[b], y[b])
+            lines.append("n %d seed %d count %d index %d per %r" % (n, seed, count, b, float(v)))
+            print(lines[-1], "%.1f s" % (time.time() - t0), flush=True)
+    write("cauchy_exact.txt", lines)
+
+
 if __name__ == "__main__":
+    if sys.argv[1:] == ["cauchy"]:
+        cauchy_exact()
+        sys.exit(0)
     square16_f64()
     square26_01()
     rect20x40_f64()

@@ -61,6 +61,8 @@ def test_null_handle_is_rejected(lib):
     rc = lib.perm_sbp(None, ctypes.addressof(a), 2, 2, 2, capi.PERM_F64, ctypes.addressof(occ), 1,
                       ctypes.addressof(out), None, None)
     assert rc == capi.PERM_EINVAL
+    rc = lib.perm_cauchy(None, ctypes.addressof(a), ctypes.addressof(a), 2, 1, ctypes.addressof(out), None, None)
+    assert rc == capi.PERM_EINVAL
     assert lib.perm_destroy(None) == capi.PERM_EINVAL
     assert lib.perm_create(None, 0) == capi.PERM_EINVAL
 

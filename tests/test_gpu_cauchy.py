@@ -1,0 +1,149 @@
+"""Parity of perm_cauchy (Borchardt's theorem, Eq. caucy_permanent, in multi-limb
+floating point) with the oracle's exact rational permanents of the same Cauchy
+matrices.  The kernel returns the permanent of the exact matrix of the given doubles
+rounded to double, so the bar is one unit in the last place of the exact value."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import GOLDEN, device
+from paper_2510_03421_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ULP = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2510_03421_gb300 import capi
+    return capi
+
+
+def gpu_cauchy(capi, dev, x, y, want_err=False):
+    import torch
+    dx = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    dy = torch.from_numpy(np.ascontiguousarray(y)).to(dev)
+    n = x.shape[-1]
+    count = x.size // n
+    err = torch.full((count,), -1.0, dtype=torch.float64, device=dev) if want_err else None
+    out = capi.perm_cauchy(dx, dy, opts={"err": err} if want_err else None)
+    torch.cuda.synchronize(dev)
+    return (out.cpu().numpy(), err.cpu().numpy()) if want_err else out.cpu().numpy()
+
+
+def exact(x, y):
+    return oracle.cauchy.permanent_borchardt(x, y)
+
+
+def within_ulp(got, ex):
+    return abs(got - float(ex)) <= ULP * abs(float(ex))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 16, 20])
+def test_small_orders_exact_value(capi, dev, n):
+    x, y = inputs.cauchy_points(n, 1200 + n, count=3)
+    got, err = gpu_cauchy(capi, dev, x, y, want_err=True)
+    for b in range(3):
+        ex = exact(x[b], y[b])
+        assert within_ulp(got[b], ex), (b, got[b], float(ex))
+        assert abs(got[b] - float(ex)) <= err[b] <= 2.0 ** -50 * abs(got[b])
+    if n <= 7:
+        C = oracle.cauchy.cauchy_matrix(x[0], y[0])
+        assert within_ulp(got[0], oracle.cauchy.permanent_definition(C))
+
+
+@pytest.mark.parametrize("n", [4, 9, 14])
+def test_interleaved_points_entries_of_both_signs(capi, dev, n):
+    g = inputs.rng(1300 + n)
+    pts = g.permutation(g.uniform(-1.0, 1.0, 2 * n))
+    x, y = pts[:n].copy(), pts[n:].copy()
+    got = gpu_cauchy(capi, dev, x[None], y[None])
+    assert within_ulp(got[0], exact(x, y))
+
+
+def golden_cases():
+    path = os.path.join(GOLDEN, "cauchy_exact.txt")
+    cases = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        kv = dict(zip(f[0::2], f[1::2]))
+        cases.append({k: (float(v) if k == "per" else int(v)) for k, v in kv.items()})
+    return cases
+
+
+def test_large_orders_against_stored_exact_values(capi, dev):
+    # orders whose exact evaluation takes the oracle minutes; values written by
+    # tests/golden/make_golden.py from oracle.cauchy alone
+    seen = set()
+    for case in golden_cases():
+        n, seed, count, b = case["n"], case["seed"], case["count"], case["index"]
+        key = (n, seed, count)
+        if key in seen:
+            continue
+        seen.add(key)
+        x, y = inputs.cauchy_points(n, seed, count=count)
+        got, err = gpu_cauchy(capi, dev, x, y, want_err=True)
+        for c in golden_cases():
+            if (c["n"], c["seed"], c["count"]) == key:
+                i = c["index"]
+                assert abs(got[i] - c["per"]) <= ULP * abs(c["per"]), (n, i, got[i], c["per"])
+                assert err[i] <= 2.0 ** -50 * abs(got[i])
+        assert np.all(np.isfinite(got)) and np.all(got > 0)  # x > y: every term is positive
+
+
+def test_host_and_device_buffers_agree_and_repeat_bit_for_bit(capi, dev):
+    x, y = inputs.cauchy_points(18, 1400, count=5)
+    a = gpu_cauchy(capi, dev, x, y)
+    host = capi.perm_cauchy(x, y)
+    b = gpu_cauchy(capi, dev, x, y)
+    assert np.array_equal(a, host) and np.array_equal(a, b)
+    one = capi.perm_cauchy(x[2], y[2])
+    assert one.shape == (1,) and one[0] == a[2]
+
+
+def test_coinciding_points_give_nan_and_a_status(capi, dev):
+    import torch
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    st = capi.ctypes.c_int(-1)
+    assert capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st)) == capi.PERM_OK  # clear
+    x, y = inputs.cauchy_points(6, 1500, count=4)
+    x[1, 3] = x[1, 0]          # repeated x: det(C) = 0
+    y[2, 5] = x[2, 2]          # infinite entry
+    x[3, 4] = np.inf
+    got = gpu_cauchy(capi, dev, x, y)
+    assert np.isfinite(got[0]) and np.all(np.isnan(got[1:]))
+    rc = capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st))
+    assert rc == capi.PERM_OK and st.value == capi.PERM_EINVAL
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_cauchy(x, y)  # host output: the status comes back from the call
+    assert e.value.status == capi.PERM_EINVAL
+
+
+def test_argument_errors(capi, dev):
+    x, y = inputs.cauchy_points(65, 1600)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_cauchy(x, y)
+    assert e.value.status == capi.PERM_ETOOBIG
+    empty = np.zeros((0, 5))
+    assert capi.perm_cauchy(empty, empty).shape == (0,)
+
+
+def test_order_64_top_of_the_range(capi, dev):
+    # at n = 64 every entry is in [2/3, 2]; per lies between 64! (2/3)^64 and 64! 2^64
+    import math
+    x, y = inputs.cauchy_points(64, 1700, count=2)
+    got = gpu_cauchy(capi, dev, x, y)
+    lo = math.lgamma(65) + 64 * math.log(2.0 / 3.0)
+    hi = math.lgamma(65) + 64 * math.log(2.0)
+    for v in got:
+        assert lo <= math.log(v) <= hi
