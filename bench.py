@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
     ap.add_argument("--batch-count", type=int, default=100000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cauchy-only", action="store_true",
+                    help="run only the Cauchy (Borchardt) leg and print its figures as one JSON line")
     return ap.parse_args()
 
 
@@ -295,6 +297,40 @@ def run_sbp(args, dev, stream, count=1000000, n=12, N=24):
             "ms_per_call": ms}
 
 
+def run_cauchy(args, dev, stream, count=1216, n=36):
+    """Cauchy permanents by Borchardt's theorem (perm_cauchy): `count` matrices
+    c_ij = 1 / (x_i - y_j) of order n with the points of the paper's accuracy tests
+    (x ~ U[0.25, 0.75], y ~ U[-0.75, -0.25]), one call per step; plus one matrix of
+    order 36 and one of order 64 alone (latency)."""
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    seed = inputs.SEED_BASE + 15
+    x, y = inputs.cauchy_points(n, seed, count=count)
+
+    def timed(xh, yh, steps):
+        dx, dy = torch.from_numpy(xh).to(dev), torch.from_numpy(yh).to(dev)
+        out = torch.empty(xh.shape[0], dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                capi.perm_cauchy(dx, dy, out=out, stream=stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                ev[k][0].record(stream)
+                capi.perm_cauchy(dx, dy, out=out, stream=stream)
+                ev[k][1].record(stream)
+            stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, out
+    ms, out = timed(x, y, args.steps)
+    ms36, _ = timed(x[:1], y[:1], args.steps)
+    x64, y64 = inputs.cauchy_points(64, seed + 1)
+    ms64, _ = timed(x64, y64, args.steps)
+    return {"workload": "%d Cauchy matrices of order %d, x ~ U[0.25,0.75], y ~ U[-0.75,-0.25], seed %d" % (
+                count, n, seed),
+            "matrices_per_s": count / (ms * 1e-3), "ms_per_call": ms, "first": float(out[0].item()),
+            "ms_one_matrix_n36": ms36, "ms_one_matrix_n64": ms64}
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
     """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
@@ -339,6 +375,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     from paper_2510_03421_gb300 import capi
 
+    if args.cauchy_only:
+        print(json.dumps(run_cauchy(args, dev, torch.cuda.Stream(dev))), flush=True)
+        return
     A, desc = workload(args.n, args.dtype)
     n = args.n
     terms = 1 << (n - 1)
@@ -476,6 +515,7 @@ def run_ours(args):
         line["batched"]["frac_of_fp64_peak"] = line["batched"]["fp64_equiv_tflops"] * 1e12 / peak_flops
         line["batched_real"] = run_batched_real(args, dev, side)
         line["sbp"] = run_sbp(args, dev, side)
+        line["cauchy"] = run_cauchy(args, dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -1247,10 +1247,11 @@ int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int6
   double* err = opts ? opts->err : nullptr;
   const size_t pts = 8 * (size_t)(n * count);
   const bool hx = !on_device(x), hy = !on_device(y), hOut = !on_device(out), hErr = err && !on_device(err);
-  int64_t grid = 2 * (int64_t)h->sms;
-  if (grid > count) grid = count;
+  int block = 0;
+  const int grid = cauchy_grid(count, h->sms, &block);
   const size_t scratch = align_up(8 * cauchy_scratch_words((int)n) * (size_t)grid);
-  const size_t need = scratch + (hx ? align_up(pts) : 0) + (hy ? align_up(pts) : 0) +
+  const size_t state = align_up(cauchy_state_bytes(count));
+  const size_t need = scratch + state + (hx ? align_up(pts) : 0) + (hy ? align_up(pts) : 0) +
                       (hOut ? align_up(8 * (size_t)count) : 0) + (hErr ? align_up(8 * (size_t)count) : 0);
   int rc = ensure_sws(h, need);
   if (rc) return rc;
@@ -1258,6 +1259,8 @@ int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int6
   char* base = static_cast<char*>(h->sws);
   uint64_t* dScratch = reinterpret_cast<uint64_t*>(base);
   base += scratch;
+  void* dState = base;
+  base += state;
   const double* dx = x;
   const double* dy = y;
   double* dOut = out;
@@ -1280,7 +1283,7 @@ int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int6
   const bool host_result = hOut || hErr;
   int* st = host_result ? call_status_word(h) : status_word(h);
   if (host_result && cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess) return PERM_ECUDA;
-  if (launch_cauchy(dx, dy, (int)n, count, dOut, dErr, dScratch, (int)grid, st, s) != cudaSuccess)
+  if (launch_cauchy(dx, dy, (int)n, count, dOut, dErr, dScratch, dState, grid, block, st, s) != cudaSuccess)
     return PERM_ECUDA;
   if (hOut && cudaMemcpyAsync(out, dOut, 8 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PERM_ECUDA;

@@ -173,14 +173,19 @@ int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dt
             int64_t count, double* dout, cudaStream_t stream, int chunk_log2, int sms, bool fp64, void* scratch);
 // Cauchy permanents by Borchardt's theorem (cauchy.cu): out[b] = per(1 / (x_i - y_j)) of
 // matrix b (x, y: count x n, device); err (or null) gets an error estimate per matrix;
-// scratch: grid * cauchy_scratch_words(n) words of device memory; status: sticky code
-// (1 = coinciding or non-finite points, 2 = precision ladder exhausted; result NaN)
+// scratch: grid * cauchy_scratch_words(n) words of device memory; state:
+// cauchy_state_bytes(count) bytes (8-byte aligned, no initial contents needed);
+// status: sticky code (1 = coinciding or non-finite points, 2 = precision ladder
+// exhausted; result NaN)
 size_t cauchy_scratch_words(int n);
+size_t cauchy_state_bytes(int64_t count);
 int cauchy_first_limbs(int n);
+int cauchy_ladder(int n, int* rungs);
 int cauchy_max_n();
 int cauchy_block();
+int cauchy_grid(int64_t count, int sms, int* block);  // blocks (and threads per block) of a launch
 cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count, double* out, double* err,
-                          uint64_t* scratch, int grid, int* status, cudaStream_t stream);
+                          uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream);
 // host orchestration of perm_batched (batched_host.cu)
 int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                 int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);
