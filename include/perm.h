@@ -125,7 +125,13 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
 
 /* Algorithm selection in place of the paper's tuned hyperplanes (Algorithm "Optimized
  * Algorithm Selection"): a cost model trained on this library's own timings picks the
- * algorithm and kernel configuration; opts->exhaustive times every candidate instead. */
+ * algorithm and kernel configuration; opts->exhaustive times every candidate instead.
+ * Structure is used first (not with opts->exhaustive): a real or complex matrix with an
+ * empty row gives 0, one whose nonzero pattern splits into independent blocks is the
+ * product of the blocks' permanents, and a dense real square matrix of order >= 24
+ * whose entries are 1/(x_i - y_j) within 2^-48 relative, all of one sign, is evaluated
+ * by Borchardt's theorem on the fitted points (perm_cauchy), the error bound widened
+ * by n 2^-48 (1 + n 2^-48) |per| for the fit. */
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
               void* stream, const perm_opts* opts);
 

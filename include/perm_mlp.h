@@ -30,7 +30,11 @@ typedef enum {
   PERM_CAND_RYSER = 1,        /* perm_ryser (real input) */
   PERM_CAND_GLYNN = 2,        /* perm_glynn, FP64 / exact integer arithmetic */
   PERM_CAND_GLYNN_FIXED = 3,  /* perm_glynn with PERM_ARITH_FIXED (real input) */
-  PERM_NCAND = 4
+  PERM_NCAND = 4,
+  PERM_CAND_CAUCHY = 8        /* not a cost-model output: a real square matrix of order >= 24 whose
+                                 entries are 1/(x_i - y_j) within 2^-48 relative, all of one sign,
+                                 is evaluated by Borchardt's theorem on the fitted points (see
+                                 perm_cauchy); the error bound then adds n 2^-48 (1 + n 2^-48) |per| */
 } perm_candidate;
 
 #define PERM_NFEATURES 12
@@ -65,9 +69,10 @@ int perm_mlp_train(const float* X, const float* T, const float* mask, int64_t ro
  * weights = NULL removes it (perm_auto then uses its built-in rule). */
 int perm_set_cost_model(perm_handle h, const float* weights, int32_t in_dim, int32_t hidden, int32_t out_dim);
 
-/* The choice perm_auto would make for this matrix (no computation): *candidate gets a
- * perm_candidate, predicted (if not null) PERM_NCAND predicted log2 seconds
- * (+inf for candidates that are not available or exceed the work cap). */
+/* The choice perm_auto would make for this matrix (no permanent is computed): *candidate
+ * gets a perm_candidate, predicted (if not null) PERM_NCAND predicted log2 seconds
+ * (+inf for candidates that are not available or exceed the work cap; all +inf for
+ * PERM_CAND_CAUCHY). */
 int perm_auto_choice(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, const perm_opts* opts,
                      int* candidate, float* predicted);
 

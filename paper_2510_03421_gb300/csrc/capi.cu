@@ -832,6 +832,7 @@ int run_candidate(Call& c, int cand) {
 
 uint64_t max_terms(const perm_opts& o) { return o.max_terms ? o.max_terms : kDefaultMaxTerms; }
 
+
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Grow the staging / scratch buffer of perm_sbp and perm_cauchy (not during capture).
@@ -848,6 +849,47 @@ int ensure_sws(perm_handle h, size_t need) {
     return PERM_ENOMEM;
   }
   h->sws_bytes = need;
+  return PERM_OK;
+}
+
+// Cauchy structure in perm_auto: real square matrices from this order on (below it a
+// sweep is as fast as the precision ladder) whose entries fit 1/(x_i - y_j) within
+// kCauchyFitTol relative, all of one sign.
+constexpr int kCauchyAutoMin = 24;
+constexpr double kCauchyFitTol = 0x1p-48;
+
+// Fit points to a dense real square operand; *yes on success, with the points left at
+// the start of the partial-record area and *rel the relative bound on per(A) - per(C').
+int cauchy_fit(const Call& c, bool* yes, double* rel) {
+  *yes = false;
+  if (c.dtype != PERM_F64 || c.m != c.n || c.n < kCauchyAutoMin) return PERM_OK;
+  double* pts = reinterpret_cast<double*>(partials_base(c.h));
+  int* flag = reinterpret_cast<int*>(pts + 128);
+  if (launch_cauchy_fit(static_cast<const double*>(c.dA), c.n, c.rs, c.cs, kCauchyFitTol, pts, pts + 64, flag,
+                        c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  int ok = 0;
+  if (cudaMemcpyAsync(&ok, flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+      cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  *yes = ok != 0;
+  const double nt = c.n * kCauchyFitTol;
+  *rel = nt * (1.0 + nt);  // >= (1 + tol)^n - 1 for n tol << 1
+  return PERM_OK;
+}
+
+// per(A) of a fitted Cauchy operand by Borchardt's theorem (points from cauchy_fit).
+int cauchy_from_fit(Call& c, double rel) {
+  int block = 0;
+  const int grid = cauchy_grid(1, c.h->sms, &block);
+  const size_t scratch = align_up(8 * cauchy_scratch_words(c.n) * (size_t)grid);
+  int rc = ensure_sws(c.h, scratch + align_up(cauchy_state_bytes(1)));
+  if (rc) return rc;
+  char* base = static_cast<char*>(c.h->sws);
+  const double* pts = reinterpret_cast<const double*>(partials_base(c.h));
+  if (launch_cauchy(pts, pts + 64, c.n, 1, static_cast<double*>(c.dOut), c.dErr, reinterpret_cast<uint64_t*>(base),
+                    base + scratch, grid, block, status_word(c.h), c.stream, rel) != cudaSuccess)
+    return PERM_ECUDA;
   return PERM_OK;
 }
 
@@ -1045,6 +1087,16 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
   rc = density_of(c, &density);
   if (rc) return rc;
   const uint64_t cap = max_terms(c.o);
+  if (!c.o.exhaustive && density == 1.0) {
+    // a Cauchy matrix up to rounding: Borchardt's theorem in O(n^3)
+    bool yes = false;
+    double rel = 0.0;
+    if ((rc = cauchy_fit(c, &yes, &rel)) != PERM_OK) return rc;
+    if (yes) {
+      if ((rc = cauchy_from_fit(c, rel)) != PERM_OK) return rc;
+      return finish(c, out_size(dtype));
+    }
+  }
   if (!c.o.exhaustive && density < 1.0) {
     // structure of the nonzero pattern: an empty row, or independent blocks
     std::vector<unsigned char> host;
@@ -1173,6 +1225,17 @@ int perm_auto_choice(perm_handle h, const void* A, int64_t m, int64_t n, int64_t
   double density = 1.0;
   rc = density_of(c, &density);
   if (rc) return rc;
+  if (!c.o.exhaustive && density == 1.0) {
+    bool yes = false;
+    double rel = 0.0;
+    if ((rc = cauchy_fit(c, &yes, &rel)) != PERM_OK) return rc;
+    if (yes) {
+      *candidate = PERM_CAND_CAUCHY;
+      if (predicted)
+        for (int k = 0; k < PERM_NCAND; ++k) predicted[k] = INFINITY;
+      return PERM_OK;
+    }
+  }
   return choose(h, c.m, c.n, density, dtype, max_terms(c.o), candidate, predicted);
 }
 

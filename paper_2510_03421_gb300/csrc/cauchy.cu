@@ -69,6 +69,48 @@ cudaError_t launch_rung_l(int L, const CauchyArgs& a, int grid, cudaStream_t str
   }
 }
 
+// Does the n x n real matrix A hold c_ij = 1 / (x_i - y_j) up to rounding?  Points fitted
+// with x_0 = 0: y_j = -1 / a_0j, x_i = 1 / a_i0 + y_0.  Accepted when every entry is
+// finite, nonzero and of the sign of a_00, |a_ij (x_i - y_j) - 1| <= tol (bounded from
+// the exact split x_i - y_j = s + e and one fused multiply-add for a_ij s - 1), and the
+// x_i and the y_j are distinct.  Then a_ij = c'_ij (1 + rho_ij), |rho_ij| <= tol, for the
+// exact Cauchy matrix C' of the fitted points, and every term of both permanents has
+// one sign, so |per(A) - per(C')| <= ((1 + tol)^n - 1) |per(C')|.
+__global__ void __launch_bounds__(kBlock) cauchy_fit_kernel(const double* __restrict__ A, int n, int64_t rs,
+                                                            int64_t cs, double tol, double* x, double* y, int* ok) {
+  __shared__ double sx[64], sy[64];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_bad = 0;
+  if (tid < n) sy[tid] = __ddiv_rn(-1.0, A[tid * cs]);
+  __syncthreads();
+  if (tid < n) sx[tid] = __dadd_rn(__ddiv_rn(1.0, A[tid * rs]), sy[0]);
+  __syncthreads();
+  const bool neg = A[0] < 0.0;
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    const double a = A[i * rs + j * cs];
+    bool bad = !isfinite(a) || a == 0.0 || (a < 0.0) != neg;
+    if (!bad) {
+      const double u = sx[i], v = -sy[j];
+      const double sum = __dadd_rn(u, v);
+      const double bv = __dsub_rn(sum, u);
+      const double e = __dadd_rn(__dsub_rn(u, __dsub_rn(sum, bv)), __dsub_rn(v, bv));
+      const double r = __fma_rn(a, sum, -1.0);
+      const double bound = __dmul_rn(__dadd_rn(::fabs(r), ::fabs(__dmul_rn(a, e))), 1.0 + 0x1p-50);
+      bad = !isfinite(sum) || !(bound <= tol);
+    }
+    if (i < j) bad |= sx[i] == sx[j] || sy[i] == sy[j];
+    if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  if (tid < n) {
+    x[tid] = sx[tid];
+    y[tid] = sy[tid];
+  }
+  if (tid == 0) *ok = !s_bad;
+}
+
 }  // namespace
 }  // namespace cauchy
 
@@ -110,10 +152,18 @@ int cauchy_grid(int64_t count, int sms, int* block) {
   return (int)(count < 2 * (int64_t)sms ? count : 2 * (int64_t)sms);
 }
 
+cudaError_t launch_cauchy_fit(const double* A, int n, int64_t rs, int64_t cs, double tol, double* x, double* y,
+                              int* ok, cudaStream_t stream) {
+  cauchy::cauchy_fit_kernel<<<1, kBlock, 0, stream>>>(A, n, rs, cs, tol, x, y, ok);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count, double* out, double* err,
-                          uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream) {
+                          uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream,
+                          double rel_extra) {
   CauchyArgs a;
   a.block = block;
+  a.rel_extra = rel_extra;
   a.x = x;
   a.y = y;
   a.n = n;

@@ -27,6 +27,7 @@ struct CauchyArgs {
   int* status;        // set to 1 (coinciding or non-finite points) or 2 (ladder exhausted)
   int last;           // this rung is the last of the ladder
   int block;          // threads per block (kBlock)
+  double rel_extra;   // added to the relative error estimate (perturbation of fitted points)
 };
 
 template <int L>
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kBlock, L <= 8 ? 2 : 1) cauchy_rung_kernel(Cau
         if (d.z || (!res.z && d.e <= res.e - 62)) {
           const double v = big_to_double(res);
           a.out[b] = v;
-          if (a.err) a.err[b] = ::fabs(big_to_double(d)) * (1.0 + 0x1p-40) + ::fabs(v) * 0x1p-53;
+          if (a.err) a.err[b] = ::fabs(big_to_double(d)) * (1.0 + 0x1p-40) + ::fabs(v) * (0x1p-53 + a.rel_extra);
           next = 2;
         }
       }

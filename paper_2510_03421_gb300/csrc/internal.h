@@ -185,7 +185,12 @@ int cauchy_max_n();
 int cauchy_block();
 int cauchy_grid(int64_t count, int sms, int* block);  // blocks (and threads per block) of a launch
 cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count, double* out, double* err,
-                          uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream);
+                          uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream,
+                          double rel_extra = 0.0);
+// fit points x, y (n each, device) to a real n x n matrix (n <= 64); *ok = 1 if every
+// entry is 1 / (x_i - y_j) within relative tol, all of one sign (see cauchy.cu)
+cudaError_t launch_cauchy_fit(const double* A, int n, int64_t rs, int64_t cs, double tol, double* x, double* y,
+                              int* ok, cudaStream_t stream);
 // host orchestration of perm_batched (batched_host.cu)
 int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                 int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);

@@ -147,3 +147,57 @@ def test_order_64_top_of_the_range(capi, dev):
     hi = math.lgamma(65) + 64 * math.log(2.0)
     for v in got:
         assert lo <= math.log(v) <= hi
+
+
+# --- perm_auto recognises a Cauchy matrix given as a dense double matrix
+
+
+def cauchy_matrix_double(x, y):
+    return 1.0 / (x[:, None] - y[None, :])
+
+
+def auto_choice(capi, A):
+    import ctypes
+    cand = ctypes.c_int(-1)
+    A = np.ascontiguousarray(A)
+    rc = capi.lib().perm_auto_choice(capi.handle(0), A.ctypes.data, A.shape[0], A.shape[1], A.shape[1],
+                                     capi.PERM_F64, None, ctypes.byref(cand), None)
+    assert rc == capi.PERM_OK
+    return cand.value
+
+
+def test_perm_auto_takes_borchardt_for_cauchy_matrices(capi, dev):
+    import torch
+    for case in golden_cases():
+        if case["count"] != 1:
+            continue
+        n = case["n"]
+        x, y = inputs.cauchy_points(n, case["seed"])
+        A = cauchy_matrix_double(x[0], y[0])
+        assert auto_choice(capi, A) == capi.PERM_CAND_CAUCHY, n
+        err = torch.zeros(1, dtype=torch.float64, device=dev)
+        out = capi.perm_auto(torch.from_numpy(A).to(dev), opts={"err": err})
+        torch.cuda.synchronize(dev)
+        got, e = float(out.item()), float(err.item())
+        # A is the exact matrix of the points rounded entrywise (two roundings: |rel| <= 2u),
+        # and every term is positive: per(A) is within n 2u of the stored per(C); the fit
+        # adds at most n 2^-48, the result's own rounding 1 ulp
+        tol = (n * 2.0 ** -52 + n * 2.0 ** -48 * 1.01 + 2.0 ** -52) * case["per"]
+        assert abs(got - case["per"]) <= tol, (n, got, case["per"])
+        assert 0 < e <= (n * 2.0 ** -48 * 1.01 + 2.0 ** -50) * got
+        host = capi.perm_auto(A)
+        assert float(host[0]) == got
+
+
+def test_perm_auto_keeps_the_general_path_off_cauchy_structure(capi, dev):
+    x, y = inputs.cauchy_points(26, 1800)
+    A = cauchy_matrix_double(x[0], y[0])
+    assert auto_choice(capi, A) == capi.PERM_CAND_CAUCHY
+    B = A.copy()
+    B[3, 7] *= 1.0 + 1e-9  # no longer 1/(x_i - y_j) within 2^-48
+    assert auto_choice(capi, B) != capi.PERM_CAND_CAUCHY
+    g = inputs.rng(1801)
+    pts = g.permutation(g.uniform(-1.0, 1.0, 52))  # Cauchy, but entries of both signs
+    assert auto_choice(capi, cauchy_matrix_double(pts[:26], pts[26:])) != capi.PERM_CAND_CAUCHY
+    x, y = inputs.cauchy_points(20, 1802)  # below the order where the ladder pays
+    assert auto_choice(capi, cauchy_matrix_double(x[0], y[0])) != capi.PERM_CAND_CAUCHY
