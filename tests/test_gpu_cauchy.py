@@ -201,3 +201,24 @@ def test_perm_auto_keeps_the_general_path_off_cauchy_structure(capi, dev):
     assert auto_choice(capi, cauchy_matrix_double(pts[:26], pts[26:])) != capi.PERM_CAND_CAUCHY
     x, y = inputs.cauchy_points(20, 1802)  # below the order where the ladder pays
     assert auto_choice(capi, cauchy_matrix_double(x[0], y[0])) != capi.PERM_CAND_CAUCHY
+
+
+def test_invariances_scaling_translation_permutation(capi, dev):
+    # c_ij(2^k x, 2^k y) = 2^-k c_ij(x, y): per scales by 2^(-k n) exactly, while det(C)
+    # and det(C o C) leave the double range by far (2^(+-k n^2)); a shift of both point
+    # sets leaves C unchanged (points on a dyadic grid, so the shift is exact); permuting
+    # the points permutes rows or columns
+    import math
+    g = inputs.rng(1900)
+    n = 8
+    x = np.round(g.uniform(0.25, 0.75, n) * 2 ** 20) / 2 ** 20
+    y = np.round(g.uniform(-0.75, -0.25, n) * 2 ** 20) / 2 ** 20
+    base = gpu_cauchy(capi, dev, x[None], y[None])[0]
+    assert within_ulp(base, exact(x, y))
+    for k in (-100, 60, 110):
+        got = gpu_cauchy(capi, dev, np.ldexp(x, k)[None], np.ldexp(y, k)[None])[0]
+        assert got == math.ldexp(base, -k * n), k
+    shifted = gpu_cauchy(capi, dev, (x + 3.0)[None], (y + 3.0)[None])[0]
+    assert shifted == base
+    p, q = g.permutation(n), g.permutation(n)
+    assert gpu_cauchy(capi, dev, x[p][None], y[q][None])[0] == base
