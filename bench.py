@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 sweep comparison")
     ap.add_argument("--batch-count", type=int, default=100000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision-only", action="store_true",
+                    help="run only the precision study (digits lost) and print it as one JSON line")
     ap.add_argument("--cauchy-only", action="store_true",
                     help="run only the Cauchy (Borchardt) leg and print its figures as one JSON line")
     return ap.parse_args()
@@ -331,6 +333,49 @@ def run_cauchy(args, dev, stream, count=1216, n=36):
             "ms_one_matrix_n36": ms36, "ms_one_matrix_n64": ms64}
 
 
+def run_precision(dev, stream, cases=((8, 8), (16, 16), (24, 24), (32, 32), (8, 16), (16, 32))):
+    """The paper's precision study (Eq. digits_lost, d = log10(|eval - true| / |true|) -
+    log10(eps)) on its three matrix families: all ones (per = n!/(n-m)!), the identity
+    padded with zero columns (per = 1) and Cauchy matrices c_ij = 1/(x_i - y_j) (square;
+    truth: perm_cauchy, Borchardt's theorem rounded to double).  Each algorithm reports
+    d and whether its stated error bound covers the error."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    eps = float(np.finfo(np.float64).eps)
+    algos = {"glynn": ("perm_glynn", capi.PERM_ARITH_AUTO), "glynn_fp64": ("perm_glynn", capi.PERM_ARITH_FP64),
+             "ryser": ("perm_ryser", capi.PERM_ARITH_AUTO)}
+
+    def digits(v, t):
+        e = abs(v - t)
+        return None if e == 0 else round(math.log10(e / abs(t)) - math.log10(eps), 2)
+
+    rows = []
+    for m, n in cases:
+        fams = [("ones", np.ones((m, n)), math.factorial(n) / math.factorial(n - m)),
+                ("identity", np.eye(m, n), 1.0)]
+        if m == n:
+            x, y = inputs.cauchy_points(n, inputs.SEED_BASE + 20 + n, draws=100)
+            dx, dy = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+            t = float(capi.perm_cauchy(dx, dy, stream=stream)[0].item())
+            fams.append(("cauchy", 1.0 / (x[0][:, None] - y[0][None, :]), t))
+        for name, A, truth in fams:
+            row = {"matrix": "%s %dx%d" % (name, m, n), "true": truth}
+            dA = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
+            for key, (fn, arith) in algos.items():
+                out = torch.empty(1, dtype=torch.float64, device=dev)
+                err = torch.empty(1, dtype=torch.float64, device=dev)
+                getattr(capi, fn)(dA, out=out, stream=stream, opts={"arith": arith, "err": err})
+                stream.synchronize()
+                v, e = float(out.item()), float(err.item())
+                row[key] = {"d": digits(v, truth), "bound_holds": (e < 0) or abs(v - truth) <= e}
+            rows.append(row)
+    return {"metric": "digits lost, Eq. digits_lost (None = exact)", "cases": rows}
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
     """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
@@ -377,6 +422,9 @@ def run_ours(args):
 
     if args.cauchy_only:
         print(json.dumps(run_cauchy(args, dev, torch.cuda.Stream(dev))), flush=True)
+        return
+    if args.precision_only:
+        print(json.dumps(run_precision(dev, torch.cuda.Stream(dev))), flush=True)
         return
     A, desc = workload(args.n, args.dtype)
     n = args.n
@@ -516,6 +564,7 @@ def run_ours(args):
         line["batched_real"] = run_batched_real(args, dev, side)
         line["sbp"] = run_sbp(args, dev, side)
         line["cauchy"] = run_cauchy(args, dev, side)
+        line["precision"] = run_precision(dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
