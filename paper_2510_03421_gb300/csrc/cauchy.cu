@@ -122,7 +122,7 @@ size_t cauchy_scratch_words(int n) { return (size_t)kWords * ((size_t)n * n + n 
 
 size_t cauchy_state_bytes(int64_t count) { return (size_t)count * (kWords * sizeof(uint64_t) + sizeof(int)); }
 
-int cauchy_first_limbs(int n) {
+static int cauchy_first_limbs(int n) {
   // the elimination loses about 7.5 bits per unit of n (measured against exact
   // rationals on the paper's point ranges); 9 n + 32 bits leave the first rung more
   // than the 62 bits the agreement test needs
@@ -135,7 +135,7 @@ int cauchy_max_n() { return 64; }
 
 // The ladder: L0, L0 + 1, then steps of 2, 4, ..., with rungs above 12 limbs (not
 // instantiated) raised to kBigLimbs, the last rung.
-int cauchy_ladder(int n, int* rungs) {
+static int cauchy_ladder(int n, int* rungs) {
   int k = 0, L = cauchy_first_limbs(n), step = 1;
   while (L <= 12) {
     rungs[k++] = L;
@@ -190,6 +190,5 @@ cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count
   return cudaSuccess;
 }
 
-int cauchy_block() { return kBlock; }
 
 }  // namespace perm

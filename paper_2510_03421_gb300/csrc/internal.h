@@ -179,10 +179,7 @@ int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dt
 // exhausted; result NaN)
 size_t cauchy_scratch_words(int n);
 size_t cauchy_state_bytes(int64_t count);
-int cauchy_first_limbs(int n);
-int cauchy_ladder(int n, int* rungs);
 int cauchy_max_n();
-int cauchy_block();
 int cauchy_grid(int64_t count, int sms, int* block);  // blocks (and threads per block) of a launch
 cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count, double* out, double* err,
                           uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream,
