@@ -10,6 +10,9 @@
  * Common argument conventions for the per-matrix entry points
  * ------------------------------------------------------------
  *   h        handle from perm_create (owns device workspace; one host thread at a time).
+ *            The workspace is shared by all calls on the handle: calls issued on
+ *            different streams through one handle must be ordered by the caller (one
+ *            stream per handle, or one handle per stream, avoids the question).
  *   A        pointer to the matrix, row-major, element (i, j) at A[i * ld + j].
  *            May be device memory or host memory (pageable or pinned); host input
  *            is copied to the handle's workspace on `stream` before the launch.
