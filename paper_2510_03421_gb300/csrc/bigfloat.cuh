@@ -261,18 +261,31 @@ __host__ __device__ __forceinline__ void big_add(Big<L>& r, const Big<L>& a, con
   r.z = 0;
 }
 
-// r = 1 / a (a != 0): a double reciprocal of the top 53 bits, then Newton steps
-// x <- x + x (1 - a x), each doubling the correct bits (from 50), until they cover 64 L.
+// r = 1 / a (a != 0): a double-double reciprocal of the top 106 bits of the mantissa
+// (one Newton step on the FP64 unit, about 2^-104 relative), then Newton steps
+// x <- x + x (1 - a x) in L limbs, each doubling the correct bits, until they cover 64 L.
 template <int L>
 __host__ __device__ __forceinline__ void big_recip(Big<L>& r, const Big<L>& a) {
-  const double top = (double)(a.m[0] >> 11) * 0x1p-53;  // in [1/2, 1)
+  const double h = (double)(a.m[0] >> 11) * 0x1p-53;  // in [1/2, 1)
+  const uint64_t next = (a.m[0] << 53) | (L > 1 ? a.m[1] >> 11 : 0);
+  const double l = (double)(next >> 11) * 0x1p-106;    // the following 53 bits
+  const double x0 = 1.0 / h;
+#ifdef __CUDA_ARCH__
+  const double e = __dsub_rn(__fma_rn(-h, x0, 1.0), __dmul_rn(l, x0));  // 1 - (h + l) x0
+  const double x1 = __dmul_rn(x0, e);
+#else
+  const double e = std::fma(-h, x0, 1.0) - l * x0;
+  const double x1 = x0 * e;
+#endif
   Big<L> x, t, one;
-  big_from_double(x, 1.0 / top);
+  big_from_double(x, x0);
+  big_from_double(t, x1);
+  big_add(x, x, t, 0);
   x.e -= a.e;
   x.s = a.s;
   big_from_double(one, 1.0);
 #pragma unroll 1
-  for (int bits = 50; bits < 64 * L + 8; bits *= 2) {
+  for (int bits = 100; bits < 64 * L + 8; bits *= 2) {
     big_mul(t, a, x);
     big_add(t, one, t, 1);
     big_mul(t, x, t);

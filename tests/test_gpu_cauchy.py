@@ -222,3 +222,22 @@ def test_invariances_scaling_translation_permutation(capi, dev):
     assert shifted == base
     p, q = g.permutation(n), g.permutation(n)
     assert gpu_cauchy(capi, dev, x[p][None], y[q][None])[0] == base
+
+
+def test_perm_auto_cauchy_strided_and_transposed_operands(capi, dev):
+    # the fit reads the operand through its strides: a view with ld > n, and the
+    # transpose (a Cauchy matrix with the roles of x and -y exchanged), give the same value
+    import torch
+    x, y = inputs.cauchy_points(30, 1850)
+    A = cauchy_matrix_double(x[0], y[0])
+    dense = capi.perm_auto(torch.from_numpy(A).to(dev))
+    big = torch.zeros((30, 37), dtype=torch.float64, device=dev)
+    big[:, 3:33] = torch.from_numpy(A).to(dev)
+    view = capi.perm_auto(big[:, 3:33])
+    tr = capi.perm_auto(torch.from_numpy(A.T.copy()).to(dev))
+    torch.cuda.synchronize(dev)
+    exact_v = float(oracle.cauchy.permanent_borchardt(x[0], y[0]))
+    tol = (30 * 2.0 ** -52 + 30 * 2.0 ** -48 * 1.01 + 2.0 ** -52) * exact_v
+    for v in (dense, view, tr):
+        assert abs(float(v.item()) - exact_v) <= tol
+    assert float(view.item()) == float(dense.item())
