@@ -504,8 +504,9 @@ def run_ours(args):
         if mixed and n in (33, 34, 35, 36) and args.dtype == "f64":
             # pipe utilisation of this kernel (N = 36 columns, 8 on the FP64 unit) from one ncu
             # capture at n = 34; DRAM traffic does not grow with the term count
-            roof["traffic"] = 148224
-            roof["traffic_source"] = "ncu dram__bytes_read+write of glynn_fx_kernel<36, 8, 0> at n = 34"
+            roof["traffic"] = 562688
+            roof["traffic_source"] = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of "
+                                      "glynn_fx_kernel<36, 8, 0> at n = 34 (profiles/glynn_fx_n36_launches.md)")
             roof["pipes_ncu"] = {"alu": 0.628, "fp64": 0.614, "fma": 0.276, "issue": 0.573,
                                  "source": "profiles/glynn_fx_mixed_n34_ncu.md"}
     else:
