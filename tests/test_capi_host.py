@@ -106,3 +106,13 @@ def test_damaged_cost_model_file_is_refused(tmp_path):
     np.savez(short, weights=w[:-3], dims=np.array(dims), meta=np.array("{}"))
     with pytest.raises(ValueError):
         costmodel.load(str(short))
+
+
+def test_paper_function_names_resolve_without_a_gpu():
+    import paper_2510_03421_gb300 as p
+    for base in ("combinatoric", "glynn", "ryser", "opt"):
+        for suffix in ("", "_square", "_rectangular"):
+            f = getattr(p, base + suffix)
+            assert callable(f) and f.__name__ == base + suffix
+    with pytest.raises(AttributeError):
+        getattr(p, "glynn_triangular")

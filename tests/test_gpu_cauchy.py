@@ -241,3 +241,15 @@ def test_perm_auto_cauchy_strided_and_transposed_operands(capi, dev):
     for v in (dense, view, tr):
         assert abs(float(v.item()) - exact_v) <= tol
     assert float(view.item()) == float(dense.item())
+
+
+def test_vanishing_permanent_of_order_two(capi, dev):
+    # x = (0, 1), y = (3/2, 3/4): C = [[-2/3, -4/3], [-2, 4]], per(C) = -8/3 + 8/3 = 0 and
+    # det(C o C) = 0; the two entries of the first row differ by a power of two, so the
+    # elimination cancels exactly and the call returns zero with a zero error estimate
+    x = np.array([[0.0, 1.0]])
+    y = np.array([[1.5, 0.75]])
+    C = oracle.cauchy.cauchy_matrix(x[0], y[0])
+    assert oracle.cauchy.permanent_definition(C) == 0
+    got, err = gpu_cauchy(capi, dev, x, y, want_err=True)
+    assert got[0] == 0.0 and err[0] == 0.0
