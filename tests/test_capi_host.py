@@ -116,3 +116,19 @@ def test_paper_function_names_resolve_without_a_gpu():
             assert callable(f) and f.__name__ == base + suffix
     with pytest.raises(AttributeError):
         getattr(p, "glynn_triangular")
+
+
+def test_cpp_interface_compiles_and_links(tmp_path):
+    # include/permanent.hpp (the paper's C++ function shapes over the C ABI) with every
+    # element type the check program uses; linked against the built library
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    from paper_2510_03421_gb300 import _build
+    lib = _build.build()
+    exe = tmp_path / "paper_api_check"
+    subprocess.check_call([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "paper_api_check.cpp"), lib, "-o", str(exe)])
+    assert exe.exists()

@@ -43,3 +43,23 @@ def test_device_tensor_input(pkg):
     A = torch.tensor(WORKED, dtype=torch.float64, device="cuda:0")
     assert pkg.opt(A) == 450.0
     assert pkg.glynn(A.T.contiguous()) == 450.0  # per(A^T) = per(A)
+
+
+def test_cpp_interface_runs(tmp_path):
+    # include/permanent.hpp: the paper's C++ shapes permanent::fn<Type, IntType>(m, n, ptr)
+    import os
+    import shutil
+    import subprocess
+    device()
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    from paper_2510_03421_gb300 import _build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = tmp_path / "paper_api_check"
+    subprocess.check_call([gxx, "-std=c++17", "-O1", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "paper_api_check.cpp"), _build.build(), "-o", str(exe)])
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert run.returncode == 0, run.stdout + run.stderr
+    lines = run.stdout.strip().splitlines()
+    assert len(lines) == 13 and all(l.startswith("ok ") for l in lines), run.stdout
