@@ -186,3 +186,26 @@ def test_tuner_keeps_results(capi, dev):
             close(capi.value(tuned, capi.PERM_C128, b), oracle.glynn(A), A)
         # the replayed graph with the kept setting computes the same sums in the same order
         assert capi.value(again, capi.PERM_C128, b) == capi.value(tuned, capi.PERM_C128, b)
+
+
+def test_bench_batch_full_size_sampled(capi, dev):
+    # the bench's batched workload at its full size (100,000 complex Haar blocks, n in
+    # 4..20, seed as in bench.py), tuned and then replayed from its CUDA graph as the
+    # bench times it; two matrices of every order checked against the oracle one by one
+    import torch
+    count = 100000
+    sizes, packed, offsets = inputs.batched_haar(count, 4, 20, inputs.SEED_BASE + 4)
+    M = sizes.astype(np.int32)
+    tp, to, tM = to_torch(dev, packed, offsets, M)
+    out = torch.empty((count, 2), dtype=torch.float64, device=dev)
+    capi.perm_batched(tp, to, tM, tM, out=out, opts=dict(exhaustive=1))
+    out.fill_(float("nan"))
+    capi.perm_batched(tp, to, tM, tM, out=out)  # graph replay with the tuned settings
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    for n in range(4, 21):
+        idx = np.nonzero(sizes == n)[0]
+        for b in (int(idx[0]), int(idx[-1])):
+            A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
+            close(complex(got[b, 0], got[b, 1]), oracle.glynn(A, prec="f64" if n > 16 else "ld"), A)

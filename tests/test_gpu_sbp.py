@@ -123,3 +123,22 @@ def test_real_arithmetics_and_nonfinite_columns(capi, dev, arith):
             else:  # (the oracle's product C P would carry NaN * 0 = NaN from column 5)
                 clean = np.nan_to_num(C)
                 close(got[k], oracle.sbp_coefficient(clean, int(occ[k]), "ld" if n < 14 else "f64"), C[:, cols])
+
+
+def test_bench_workload_full_size_sampled(capi, dev):
+    # the bench's SBP workload at its full size (one 12 x 24 real matrix, 1,000,000
+    # bitstrings with 12 of 24 states occupied, built as in bench.py), 64 sampled
+    # coefficients against the oracle one by one
+    import torch
+    n, N, count = 12, 24, 1000000
+    g = inputs.rng(inputs.SEED_BASE + 7)
+    C = g.uniform(-1.0, 1.0, (n, N))
+    cols = np.argsort(g.random((count, N)), axis=1)[:, :n]
+    occ = np.bitwise_or.reduce(np.left_shift(np.uint64(1), cols.astype(np.uint64)), axis=1)
+    out = capi.perm_sbp(torch.from_numpy(C).to(dev), torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    for k in np.linspace(0, count - 1, 64).astype(int):
+        M = C[:, [j for j in range(N) if (int(occ[k]) >> j) & 1]]
+        close(got[k], oracle.sbp_coefficient(C, int(occ[k])), M)
