@@ -369,8 +369,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
                 int64_t count, int dtype, void* out, cudaStream_t s, const void* opts_v) {
   const perm_opts* opts = static_cast<const perm_opts*>(opts_v);
   if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
-  if (dtype != PERM_F64 && dtype != PERM_C128)
-    return (dtype == PERM_U8 || dtype == PERM_I64 || dtype == PERM_CI64) ? PERM_EUNSUPPORTED : PERM_EINVAL;
+  if (dtype != PERM_F64 && dtype != PERM_C128) return dtype == PERM_CI64 ? PERM_EUNSUPPORTED : PERM_EINVAL;
   if (count == 0) return PERM_OK;
   if (count > (1ll << 30)) return PERM_ETOOBIG;
   const int W = dtype == PERM_C128 ? 2 : 1;
@@ -536,6 +535,105 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
       return PERM_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
   }
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
+int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                    int64_t count, int dtype, void* out, int* status, cudaStream_t s) {
+  if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
+  if (count == 0) return PERM_OK;
+  if (count > (1ll << 30)) return PERM_ETOOBIG;
+  std::vector<int64_t> hoff(count);
+  std::vector<int32_t> hM(count), hN(count);
+  const bool dev_off = on_device(offsets), dev_M = on_device(M), dev_N = on_device(N);
+  if (dev_off || dev_M || dev_N) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  if (cudaMemcpy(hoff.data(), offsets, 8 * count, dev_off ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) !=
+          cudaSuccess ||
+      cudaMemcpy(hM.data(), M, 4 * count, dev_M ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess ||
+      cudaMemcpy(hN.data(), N, 4 * count, dev_N ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) != cudaSuccess)
+    return PERM_ECUDA;
+  // matrices by padded order: lists of indices, one launch per class
+  const int pads[4] = {8, 16, 24, 32};
+  std::vector<int32_t> lists[4];
+  int64_t elems = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    if (hM[b] < 0 || hN[b] < 0 || hoff[b] < 0) return PERM_EINVAL;
+    const int n = order_of(hM[b], hN[b]);
+    if (n > batched_int_max_n()) return PERM_ETOOBIG;
+    elems = std::max<int64_t>(elems, hoff[b] + (int64_t)hM[b] * hN[b]);
+    const int np = batched_int_class(n);
+    for (int c = 0; c < 4; ++c)
+      if (pads[c] == np) lists[c].push_back((int32_t)b);
+  }
+  const size_t es = dtype == PERM_U8 ? 1 : 8;
+  const bool host_packed = !on_device(packed), host_out = !on_device(out);
+  const bool host_sizes = !dev_off || !dev_M || !dev_N;
+  size_t at = 0, packed_at = 0, out_at = 0, sizes_at = 0, list_at = 0;
+  if (host_packed) {
+    packed_at = at;
+    at = align256(at + es * (size_t)elems);
+  }
+  if (host_out) {
+    out_at = at;
+    at = align256(at + 16 * (size_t)count);
+  }
+  if (host_sizes) {
+    sizes_at = at;
+    at = align256(at + 16 * (size_t)count);
+  }
+  list_at = at;
+  at = align256(at + 4 * (size_t)count);
+  int rc = ensure_bws(h, at);
+  if (rc) return rc;
+  // the batch workspace is about to hold these operands instead of a float plan
+  if (h->cache.valid) {
+    cudaGraphExecDestroy(h->cache.exec);
+    h->cache.valid = false;
+  }
+  char* base = static_cast<char*>(h->bws);
+  const void* dpacked = packed;
+  unsigned long long* dout = static_cast<unsigned long long*>(out);
+  const int64_t* doff = offsets;
+  const int32_t* dM = M;
+  const int32_t* dN = N;
+  if (host_packed) {
+    if (cudaMemcpyAsync(base + packed_at, packed, es * (size_t)elems, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PERM_ECUDA;
+    dpacked = base + packed_at;
+  }
+  if (host_out) dout = reinterpret_cast<unsigned long long*>(base + out_at);
+  if (host_sizes) {
+    char* sz = base + sizes_at;
+    if (cudaMemcpyAsync(sz, hoff.data(), 8 * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sz + 8 * count, hM.data(), 4 * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(sz + 12 * count, hN.data(), 4 * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PERM_ECUDA;
+    doff = reinterpret_cast<const int64_t*>(sz);
+    dM = reinterpret_cast<const int32_t*>(sz + 8 * count);
+    dN = reinterpret_cast<const int32_t*>(sz + 12 * count);
+  }
+  std::vector<int32_t> all;
+  all.reserve(count);
+  size_t first[4];
+  for (int c = 0; c < 4; ++c) {
+    first[c] = all.size();
+    all.insert(all.end(), lists[c].begin(), lists[c].end());
+  }
+  int32_t* dlist = reinterpret_cast<int32_t*>(base + list_at);
+  if (cudaMemcpyAsync(dlist, all.data(), 4 * all.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return PERM_ECUDA;
+  for (int c = 0; c < 4; ++c) {
+    if (lists[c].empty()) continue;
+    if (launch_batched_int(dpacked, doff, dM, dN, dlist + first[c], (int)lists[c].size(), dtype, pads[c], dout,
+                           status, h->sms, s) != cudaSuccess)
+      return PERM_ECUDA;
+  }
+  if (host_out && cudaMemcpyAsync(out, dout, 16 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PERM_ECUDA;
+  // pageable host vectors above were copied asynchronously: finish before they go away
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
   return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 

@@ -1243,7 +1243,26 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
                  int64_t count, int dtype, void* out, void* stream, const perm_opts* opts) {
   if (!h) return PERM_EINVAL;
   if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
-  return batched_run(h, packed, offsets, M, N, count, dtype, out, static_cast<cudaStream_t>(stream), opts);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dtype == PERM_U8 || dtype == PERM_I64) {
+    // exact integer batches: one warp per matrix; the range check reports like the
+    // single-matrix calls (returned for host output, kept for perm_device_status else)
+    if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
+    if (count == 0) return PERM_OK;
+    int rc = ensure_ws(h, kWsDefault, s);
+    if (rc) return rc;
+    const bool host_out = !on_device(out);
+    int* st = host_out ? call_status_word(h) : status_word(h);
+    if (host_out && cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess) return PERM_ECUDA;
+    rc = batched_int_run(h, packed, offsets, M, N, count, dtype, out, st, s);
+    if (rc || !host_out) return rc;
+    int dev_status = 0;
+    if (cudaMemcpyAsync(&dev_status, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return PERM_ECUDA;
+    return dev_status;
+  }
+  return batched_run(h, packed, offsets, M, N, count, dtype, out, s, opts);
 }
 
 int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,

@@ -192,6 +192,16 @@ cudaError_t launch_cauchy_fit(const double* A, int n, int64_t rs, int64_t cs, do
 int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                 int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);
 void batched_release(perm_handle_s* h);
+// exact batched permanents of integer matrices (batched_int.cu; host side in
+// batched_host.cu): out gets an int128 {low, high} per matrix; status: 3 if some matrix
+// failed the a-priori range check
+int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                    int64_t count, int dtype, void* out, int* status, cudaStream_t s);
+int batched_int_class(int n);  // padded order 8, 16, 24 or 32 (0 above)
+int batched_int_max_n();
+cudaError_t launch_batched_int(const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
+                               const int32_t* list, int count, int dtype, int npad, unsigned long long* out,
+                               int* status, int sms, cudaStream_t stream);
 
 // --- final reductions (reduce.cu)
 // Sum `nrec` real records in a fixed order, scale by 2^-pow2 / fact (fact = (n-m)!,

@@ -209,3 +209,82 @@ def test_bench_batch_full_size_sampled(capi, dev):
         for b in (int(idx[0]), int(idx[-1])):
             A = packed[offsets[b]: offsets[b] + n * n].reshape(n, n)
             close(complex(got[b, 0], got[b, 1]), oracle.glynn(A, prec="f64" if n > 16 else "ld"), A)
+
+
+# --- exact integer batches (one warp per matrix, int128)
+
+
+def int_batch(seed, count, kind):
+    g = inputs.rng(seed)
+    mats = []
+    for k in range(count):
+        m, n = int(g.integers(0, 11)), int(g.integers(1, 11))
+        if kind == "u8":
+            mats.append((g.random((m, n)) < 0.6).astype(np.uint8))
+        else:
+            mats.append(g.integers(-3, 4, (m, n)).astype(np.int64))
+    return mats
+
+
+@pytest.mark.parametrize("kind", ["u8", "i64"])
+def test_integer_batch_exact_against_oracle(capi, dev, kind):
+    import torch
+    mats = int_batch(9950 if kind == "u8" else 9951, 300, kind)
+    dtype = np.uint8 if kind == "u8" else np.int64
+    packed, offsets, M, N = pack(mats, dtype)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN)
+    torch.cuda.synchronize(dev)
+    code = capi.PERM_U8 if kind == "u8" else capi.PERM_I64
+    got = results(capi, out, code, len(mats))
+    for b, A in enumerate(mats):
+        want = oracle.glynn(A.astype(np.int64))
+        assert got[b] == want, (b, A.shape, got[b], want)
+    host = capi.perm_batched(packed, offsets, M, N)  # host buffers: same results
+    assert results(capi, host, code, len(mats)) == got
+
+
+def test_integer_batch_larger_orders_and_closed_forms(capi, dev):
+    import math
+    import torch
+    g = inputs.rng(9960)
+    mats = [np.ones((24, 24), np.uint8), np.ones((12, 20), np.uint8), np.ones((20, 12), np.uint8)]
+    blocks = [(g.random((8, 8)) < 0.5).astype(np.uint8) for _ in range(2)]
+    bd = np.zeros((16, 16), np.uint8)  # block diagonal: the product of the blocks' permanents
+    bd[:8, :8], bd[8:, 8:] = blocks
+    mats.append(bd)
+    for n in (14, 18, 20):
+        mats.append((g.random((n, n)) < 0.5).astype(np.uint8))
+    packed, offsets, M, N = pack(mats, np.uint8)
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN)
+    torch.cuda.synchronize(dev)
+    got = results(capi, out, capi.PERM_U8, len(mats))
+    assert got[0] == math.factorial(24)
+    assert got[1] == math.factorial(20) // math.factorial(8) == got[2]
+    assert got[3] == oracle.subset_dp(blocks[0].astype(np.int64)) * oracle.subset_dp(blocks[1].astype(np.int64))
+    for b in range(4, len(mats)):
+        assert got[b] == oracle.subset_dp(mats[b].astype(np.int64))
+
+
+def test_integer_batch_range_check(capi, dev):
+    import torch
+    big = np.full((6, 6), 10 ** 12, dtype=np.int64)  # 2^5 6! 1e72 does not fit int128
+    small = np.eye(3, dtype=np.int64)
+    packed, offsets, M, N = pack([small, big], np.int64)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_batched(packed, offsets, M, N)  # host output: the status comes back
+    assert e.value.status == capi.PERM_EOVERFLOW
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    st = capi.ctypes.c_int(-1)
+    assert capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st)) == capi.PERM_OK
+    tp, to, tM, tN = to_torch(dev, packed, offsets, M, N)
+    out = capi.perm_batched(tp, to, tM, tN)
+    assert capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st)) == capi.PERM_OK
+    assert st.value == capi.PERM_EOVERFLOW
+    assert capi.value(out, capi.PERM_I64, 0) == 1
+    g = np.zeros((1, 33), np.uint8)
+    p2, o2, M2, N2 = pack([g], np.uint8)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_batched(p2, o2, M2, N2)
+    assert e.value.status == capi.PERM_ETOOBIG
