@@ -148,11 +148,11 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
  * PERM_ARITH_FP64; opts->exhaustive tunes the launch settings (and whether part of
  * each product goes to the FP64 unit: forced on by PERM_ARITH_MIXED, off by
  * PERM_ARITH_FIXED) on a sample and keeps them for batches of the same sizes.
- * Integer matrices (PERM_U8, PERM_I64; max(M[b], N[b]) <= 32) are computed exactly,
- * one warp per matrix (Glynn, int128 modulo 2^128, results as for perm_glynn); a
- * matrix whose a-priori bound reaches 2^126.5 raises PERM_EOVERFLOW, returned by the
- * call when out is host memory, else kept for perm_device_status; no graph, no tuner.
- * PERM_CI64 returns PERM_EUNSUPPORTED. */
+ * Integer matrices (PERM_U8, PERM_I64, PERM_CI64; max(M[b], N[b]) <= 32) are computed
+ * exactly, one warp per matrix (Glynn, int128 modulo 2^128 per part, results laid out
+ * as for perm_glynn); a matrix whose a-priori bound reaches 2^126.5 raises
+ * PERM_EOVERFLOW, returned by the call when out is host memory, else kept for
+ * perm_device_status; no graph, no tuner. */
 int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                  int64_t count, int dtype, void* out, void* stream, const perm_opts* opts);
 

@@ -329,6 +329,25 @@ def _gaussian_out(dev):
     return np.zeros(4, dtype=np.int64)
 
 
+def perm_batched_gaussian(packed, offsets, M, N, out=None, stream=None):
+    """Exact permanents of many Gaussian-integer matrices: packed holds (re, im) int64
+    pairs (matrix b's M[b] x N[b] entries from pair offsets[b] on); out gets two int128
+    (real, imaginary) per matrix, read with value(out, PERM_CI64, b)."""
+    dev = packed.device if _is_torch(packed) and packed.is_cuda else None
+    count = len(offsets)
+    if out is None:
+        if dev is not None:
+            import torch
+            out = torch.zeros((count, 4), dtype=torch.int64, device=dev)
+        else:
+            out = np.zeros((count, 4), dtype=np.int64)
+    rc = lib().perm_batched(handle(_device_index(dev)), _ptr(packed), _ptr(offsets), _ptr(M), _ptr(N), count,
+                            PERM_CI64, _ptr(out), _stream(dev, stream), None)
+    if rc:
+        raise PermError(rc, "perm_batched")
+    return out
+
+
 def perm_glynn_gaussian(re, im, out=None, stream=None, opts=None):
     """Exact permanent of the Gaussian-integer matrix re + i im (int64 parts): out holds
     two int128 (real, imaginary); read it with value(out, PERM_CI64)."""

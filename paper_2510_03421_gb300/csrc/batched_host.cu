@@ -369,7 +369,7 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
                 int64_t count, int dtype, void* out, cudaStream_t s, const void* opts_v) {
   const perm_opts* opts = static_cast<const perm_opts*>(opts_v);
   if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;
-  if (dtype != PERM_F64 && dtype != PERM_C128) return dtype == PERM_CI64 ? PERM_EUNSUPPORTED : PERM_EINVAL;
+  if (dtype != PERM_F64 && dtype != PERM_C128) return PERM_EINVAL;
   if (count == 0) return PERM_OK;
   if (count > (1ll << 30)) return PERM_ETOOBIG;
   const int W = dtype == PERM_C128 ? 2 : 1;
@@ -567,7 +567,8 @@ int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets
     for (int c = 0; c < 4; ++c)
       if (pads[c] == np) lists[c].push_back((int32_t)b);
   }
-  const size_t es = dtype == PERM_U8 ? 1 : 8;
+  const size_t es = dtype == PERM_U8 ? 1 : dtype == PERM_CI64 ? 16 : 8;
+  const size_t os = dtype == PERM_CI64 ? 32 : 16;  // bytes of one result
   const bool host_packed = !on_device(packed), host_out = !on_device(out);
   const bool host_sizes = !dev_off || !dev_M || !dev_N;
   size_t at = 0, packed_at = 0, out_at = 0, sizes_at = 0, list_at = 0;
@@ -577,7 +578,7 @@ int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets
   }
   if (host_out) {
     out_at = at;
-    at = align256(at + 16 * (size_t)count);
+    at = align256(at + os * (size_t)count);
   }
   if (host_sizes) {
     sizes_at = at;
@@ -630,7 +631,7 @@ int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets
                            status, h->sms, s) != cudaSuccess)
       return PERM_ECUDA;
   }
-  if (host_out && cudaMemcpyAsync(out, dout, 16 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (host_out && cudaMemcpyAsync(out, dout, os * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PERM_ECUDA;
   // pageable host vectors above were copied asynchronously: finish before they go away
   if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;

@@ -1244,7 +1244,7 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
   if (!h) return PERM_EINVAL;
   if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (dtype == PERM_U8 || dtype == PERM_I64) {
+  if (dtype == PERM_U8 || dtype == PERM_I64 || dtype == PERM_CI64) {
     // exact integer batches: one warp per matrix; the range check reports like the
     // single-matrix calls (returned for host output, kept for perm_device_status else)
     if (count < 0 || (count > 0 && (!packed || !offsets || !M || !N || !out))) return PERM_EINVAL;

@@ -193,8 +193,8 @@ int batched_run(perm_handle_s* h, const void* packed, const int64_t* offsets, co
                 int64_t count, int dtype, void* out, cudaStream_t stream, const void* opts);
 void batched_release(perm_handle_s* h);
 // exact batched permanents of integer matrices (batched_int.cu; host side in
-// batched_host.cu): out gets an int128 {low, high} per matrix; status: 3 if some matrix
-// failed the a-priori range check
+// batched_host.cu): out gets an int128 {low, high} per matrix (Gaussian integers: two,
+// real then imaginary); status: 3 if some matrix failed the a-priori range check
 int batched_int_run(perm_handle_s* h, const void* packed, const int64_t* offsets, const int32_t* M, const int32_t* N,
                     int64_t count, int dtype, void* out, int* status, cudaStream_t s);
 int batched_int_class(int n);  // padded order 8, 16, 24 or 32 (0 above)

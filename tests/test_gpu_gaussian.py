@@ -93,3 +93,27 @@ def test_overflow_and_refusals(capi, dev):
     for name in ("perm_ryser", "perm_combinatoric", "perm_auto"):
         rc = getattr(L, name)(h, G.ctypes.data, 4, 4, 4, capi.PERM_CI64, out.ctypes.data, None, None)
         assert rc == capi.PERM_EUNSUPPORTED, name
+
+
+def test_gaussian_batch_exact_against_oracle(capi, dev):
+    # perm_batched with PERM_CI64: one warp per matrix, two int128 parts per result
+    import torch
+    g = inputs.rng(9970)
+    mats = []
+    for k in range(120):
+        m, n = int(g.integers(0, 10)), int(g.integers(1, 10))
+        mats.append((g.integers(-2, 3, (m, n)), g.integers(-2, 3, (m, n))))
+    mats.append((np.ones((16, 16), np.int64), np.zeros((16, 16), np.int64)))  # per = 16!
+    offsets = np.zeros(len(mats), np.int64)
+    offsets[1:] = np.cumsum([re.size for re, _ in mats])[:-1]
+    packed = np.concatenate([np.stack([re, im], -1).reshape(-1) for re, im in mats] + [np.zeros(2, np.int64)])
+    M = np.array([re.shape[0] for re, _ in mats], np.int32)
+    N = np.array([re.shape[1] for re, _ in mats], np.int32)
+    tp, to, tM, tN = (torch.from_numpy(a).to(dev) for a in (packed, offsets, M, N))
+    out = capi.perm_batched_gaussian(tp, to, tM, tN)
+    torch.cuda.synchronize(dev)
+    for b, (re, im) in enumerate(mats):
+        assert capi.value(out, capi.PERM_CI64, b) == oracle.glynn_gaussian(re, im), (b, re.shape)
+    assert capi.value(out, capi.PERM_CI64, len(mats) - 1) == (math.factorial(16), 0)
+    host = capi.perm_batched_gaussian(packed, offsets, M, N)
+    assert all(capi.value(host, capi.PERM_CI64, b) == capi.value(out, capi.PERM_CI64, b) for b in range(len(mats)))
