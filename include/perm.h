@@ -51,8 +51,9 @@ typedef enum {
   PERM_U8 = 2,   /* uint8 entries (0/1 biadjacency matrices), exact integer result */
   PERM_I64 = 3,  /* int64 entries, exact integer result */
   PERM_CI64 = 4  /* Gaussian integers: interleaved (re, im) int64 pairs, exact result as two
-                    int128 (real part, then imaginary part; 32 bytes); perm_glynn and
-                    perm_glynn_partial only, n <= 32 */
+                    int128 (real part, then imaginary part; 32 bytes); perm_glynn,
+                    perm_glynn_partial, perm_auto (which takes Glynn) and perm_batched,
+                    n <= 32; perm_ryser and perm_combinatoric return PERM_EUNSUPPORTED */
 } perm_dtype;
 
 typedef enum {

@@ -1075,7 +1075,7 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
               const perm_opts* opts) {
   Call c;
-  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
+  if (dtype == PERM_CI64) return perm_glynn(h, A, m, n, ld, dtype, out, stream, opts);  // the one algorithm
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {
@@ -1214,7 +1214,15 @@ int perm_auto_choice(perm_handle h, const void* A, int64_t m, int64_t n, int64_t
                      int* candidate, float* predicted) {
   if (!candidate) return PERM_EINVAL;
   Call c;
-  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;
+  if (dtype == PERM_CI64) {  // Gaussian integers: Glynn is the one algorithm
+    double dummy[4];
+    int rc = prepare(c, h, A, m, n, ld, dtype, dummy, nullptr, opts, true);
+    if (rc) return rc;
+    *candidate = PERM_CAND_GLYNN;
+    if (predicted)
+      for (int k = 0; k < PERM_NCAND; ++k) predicted[k] = INFINITY;
+    return PERM_OK;
+  }
   double dummy_out[2];
   int rc = prepare(c, h, A, m, n, ld, dtype, dummy_out, nullptr, opts, true);
   if (rc) return rc;

@@ -90,9 +90,12 @@ def test_overflow_and_refusals(capi, dev):
     out = np.zeros(4, dtype=np.int64)
     L = capi.lib()
     h = capi.handle(0)
-    for name in ("perm_ryser", "perm_combinatoric", "perm_auto"):
+    for name in ("perm_ryser", "perm_combinatoric"):
         rc = getattr(L, name)(h, G.ctypes.data, 4, 4, 4, capi.PERM_CI64, out.ctypes.data, None, None)
         assert rc == capi.PERM_EUNSUPPORTED, name
+    # perm_auto takes Glynn, the one algorithm for Gaussian integers: per(J_4 (1 + i)) = 24 (1 + i)^4
+    assert L.perm_auto(h, G.ctypes.data, 4, 4, 4, capi.PERM_CI64, out.ctypes.data, None, None) == capi.PERM_OK
+    assert capi.value(out, capi.PERM_CI64) == (-96, 0)
 
 
 def test_gaussian_batch_exact_against_oracle(capi, dev):
