@@ -52,8 +52,8 @@ typedef enum {
   PERM_I64 = 3,  /* int64 entries, exact integer result */
   PERM_CI64 = 4  /* Gaussian integers: interleaved (re, im) int64 pairs, exact result as two
                     int128 (real part, then imaginary part; 32 bytes); perm_glynn,
-                    perm_glynn_partial, perm_auto (which takes Glynn) and perm_batched,
-                    n <= 32; perm_ryser and perm_combinatoric return PERM_EUNSUPPORTED */
+                    perm_glynn_partial, perm_auto (which takes Glynn) and perm_batched
+                    with n <= 32, perm_ryser with m <= 32, perm_combinatoric */
 } perm_dtype;
 
 typedef enum {

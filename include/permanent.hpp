@@ -12,7 +12,7 @@
  *
  * Type: double, float, std::complex<double>, std::complex<float>, an integer type
  * (computed exactly in int128: uint8_t / bool as PERM_U8, other integers as int64),
- * or std::complex of a signed integer type (Gaussian integers, exact; glynn and opt).
+ * or std::complex of a signed integer type (Gaussian integers, exact).
  * result_t<Type, void> is double (std::complex<double> for complex Type); with an
  * integer Type, IntType may name an integer return type (std::complex<IntType> for
  * complex integer Type), filled from the exact result: a value that does not fit

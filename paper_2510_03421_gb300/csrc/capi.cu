@@ -526,10 +526,11 @@ int ryser_other(Call& c) {
   const uint64_t terms = 1ull << c.n;
   if (terms > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
   if (c.dtype == PERM_C128 && c.m > 40) return PERM_EUNSUPPORTED;
+  if (c.dtype == PERM_CI64 && c.m > 32) return PERM_ETOOBIG;
   const int block = c.dtype == PERM_C128 ? 128 : 256;
   if (c.o.block > block) return PERM_EINVAL;
   int bps = ryser_ext_blocks_per_sm(c.m, c.n, c.dtype, c.o.block ? c.o.block : block);
-  const size_t rec = c.dtype == PERM_C128 ? kCplxRecord * 8 : kIntRecord * 8;
+  const size_t rec = c.dtype == PERM_C128 ? kCplxRecord * 8 : (c.dtype == PERM_CI64 ? 2 : 1) * kIntRecord * 8;
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, rec);
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, 0, terms, 14);
@@ -561,8 +562,11 @@ int ryser_other(Call& c) {
                            nullptr, false, c.stream);
     if (e == cudaSuccess && c.dErr) e = launch_write_double(-1.0, c.dErr, c.stream);
   } else {
-    e = launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, 0, 0,
-                          static_cast<unsigned long long*>(c.dOut), false, c.stream);
+    const unsigned long long* recs = static_cast<const unsigned long long*>(a.partials);
+    unsigned long long* out = static_cast<unsigned long long*>(c.dOut);
+    e = launch_finish_int(recs, lc.grid, 0, 0, out, false, c.stream);
+    if (e == cudaSuccess && c.dtype == PERM_CI64)  // imaginary parts after the real ones
+      e = launch_finish_int(recs + kIntRecord * lc.grid, lc.grid, 0, 0, out + 2, false, c.stream);
     if (e == cudaSuccess && c.dErr) e = cudaMemsetAsync(c.dErr, 0, sizeof(double), c.stream);
   }
   return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
@@ -578,7 +582,9 @@ int combinatoric_run(Call& c) {
   const int block = 128;
   if (c.o.block > 128) return PERM_EINVAL;
   int bps = combinatoric_blocks_per_sm(c.m, c.n, c.dtype, c.o.block ? c.o.block : block);
-  const size_t rec = (c.dtype == PERM_F64) ? kRealRecord * 8 : (c.dtype == PERM_C128 ? kCplxRecord * 8 : kIntRecord * 8);
+  const size_t rec = (c.dtype == PERM_F64)    ? kRealRecord * 8
+                     : (c.dtype == PERM_C128) ? kCplxRecord * 8
+                                              : (c.dtype == PERM_CI64 ? 2 : 1) * kIntRecord * 8;
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, ~0ull >> 1, 1, rec);
   lc.stream = c.stream;
   const uint64_t threads = (uint64_t)lc.grid * lc.block;
@@ -590,6 +596,12 @@ int combinatoric_run(Call& c) {
   }
   if (!c.o.grid && prefixes < threads) lc.grid = (int)((prefixes + lc.block - 1) / lc.block);
   SweepArgs a = sweep_args(c, 0, 0, 0);
+  const bool integer = c.dtype == PERM_U8 || c.dtype == PERM_I64 || c.dtype == PERM_CI64;
+  if (integer) {  // the sum of products is exact while per(|A|) < 2^126.5
+    int* st = c.hOut ? call_status_word(c.h) : status_word(c.h);
+    if (c.hOut && cudaMemsetAsync(st, 0, sizeof(int), c.stream) != cudaSuccess) return PERM_ECUDA;
+    if (launch_int_bound(c.dA, c.dtype, c.m, c.n, c.rs, c.cs, st, c.stream, false) != cudaSuccess) return PERM_ECUDA;
+  }
   if (launch_combinatoric(a, c.dtype, depth, prefixes, lc) != cudaSuccess) return PERM_ECUDA;
   if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
   cudaError_t e;
@@ -599,9 +611,13 @@ int combinatoric_run(Call& c) {
   else if (c.dtype == PERM_C128)
     e = launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, 0, 0, 0.0, static_cast<double*>(c.dOut),
                            nullptr, false, c.stream);
-  else
-    e = launch_finish_int(static_cast<const unsigned long long*>(a.partials), lc.grid, 0, 0,
-                          static_cast<unsigned long long*>(c.dOut), false, c.stream);
+  else {
+    const unsigned long long* recs = static_cast<const unsigned long long*>(a.partials);
+    unsigned long long* out = static_cast<unsigned long long*>(c.dOut);
+    e = launch_finish_int(recs, lc.grid, 0, 0, out, false, c.stream);
+    if (e == cudaSuccess && c.dtype == PERM_CI64)  // imaginary parts after the real ones
+      e = launch_finish_int(recs + kIntRecord * lc.grid, lc.grid, 0, 0, out + 2, false, c.stream);
+  }
   return e == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
@@ -1040,7 +1056,6 @@ int perm_ryser_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64
 int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out, void* stream,
                const perm_opts* opts) {
   Call c;
-  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {
@@ -1059,7 +1074,6 @@ int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
 int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
                       void* stream, const perm_opts* opts) {
   Call c;
-  if (dtype == PERM_CI64) return PERM_EUNSUPPORTED;  // Gaussian integers: Glynn only
   int rc = prepare(c, h, A, m, n, ld, dtype, out, stream, opts, true);
   if (rc) return rc;
   if (c.m == 0) {

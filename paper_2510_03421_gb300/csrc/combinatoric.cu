@@ -9,7 +9,8 @@
 // entries prune whole subtrees.  The search evaluates each subtree bottom-up
 // (value(row k) = sum over free columns c of a_kc * value(row k+1)), so rounding
 // grows with the depth of the tree, not with the number of leaves.  Prefix values are
-// combined in a Kahan sum (real, complex) or modulo 2^128 (integer).
+// combined in a Kahan sum (real, complex) or modulo 2^128 (integer; Gaussian integers
+// per part).
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -60,6 +61,28 @@ struct IntF {
   __device__ static T mul(T a, T b) { return a * b; }
   __device__ static T fma(T a, T b, T c) { return a * b + c; }
   __device__ static T add(T a, T b) { return a + b; }
+};
+
+// Gaussian integers: both parts modulo 2^128
+struct GaussT {
+  u128 re, im;
+};
+
+struct GaussF {
+  typedef GaussT T;
+  __device__ static T zero() { return T{0, 0}; }
+  __device__ static T one() { return T{1, 0}; }
+  __device__ static T load(const void* A, int64_t e) {
+    const long long* p = static_cast<const long long*>(A) + 2 * e;
+    return T{(u128)(__int128)p[0], (u128)(__int128)p[1]};
+  }
+  __device__ static bool is_zero(T x) { return x.re == 0 && x.im == 0; }
+  __device__ static T mul(T a, T b) { return T{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+  __device__ static T fma(T a, T b, T c) {
+    const T p = mul(a, b);
+    return T{p.re + c.re, p.im + c.im};
+  }
+  __device__ static T add(T a, T b) { return T{a.re + b.re, a.im + b.im}; }
 };
 
 constexpr int kMaxN = 64;
@@ -169,7 +192,25 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
   }
 
   // block reduction into one record per block
-  if constexpr (std::is_same_v<T, u128>) {
+  if constexpr (std::is_same_v<T, GaussT>) {
+    // real parts at record blockIdx.x, imaginary parts at gridDim.x + blockIdx.x
+    __shared__ u128 part[2][128];
+    part[0][threadIdx.x] = acc.re;
+    part[1][threadIdx.x] = acc.im;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u128 tr = 0, ti = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) {
+        tr += part[0][i];
+        ti += part[1][i];
+      }
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials);
+      rec[(size_t)blockIdx.x * kIntRecord] = (unsigned long long)tr;
+      rec[(size_t)blockIdx.x * kIntRecord + 1] = (unsigned long long)(tr >> 64);
+      rec[(size_t)(gridDim.x + blockIdx.x) * kIntRecord] = (unsigned long long)ti;
+      rec[(size_t)(gridDim.x + blockIdx.x) * kIntRecord + 1] = (unsigned long long)(ti >> 64);
+    }
+  } else if constexpr (std::is_same_v<T, u128>) {
     __shared__ u128 part[128];
     part[threadIdx.x] = acc;
     __syncthreads();
@@ -210,11 +251,12 @@ void* pick(int dtype) {
     case 1: return (void*)combinatoric_kernel<CplxF>;
     case 2: return (void*)combinatoric_kernel<IntF<unsigned char>>;
     case 3: return (void*)combinatoric_kernel<IntF<long long>>;
+    case 4: return (void*)combinatoric_kernel<GaussF>;
     default: return nullptr;
   }
 }
 
-size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : 16; }
+size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : dtype == 4 ? 32 : 16; }
 
 }  // namespace
 

@@ -378,7 +378,11 @@ __device__ __forceinline__ double mag_of(const void* A, int dtype, int64_t e) {
   return fabs((double)p[e]);
 }
 
-__global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status) {
+// glynn: the bound of the Glynn and Ryser sums, 2^(n-1) (n-m)! per(|A|) (Bregman for 0/1
+// input, and the column sums' headroom); otherwise that of the plain sum of products
+// (the combinatoric algorithm), per(|A|) <= prod_i sum_j |a_ij|.
+__global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
+                                 bool glynn) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double ln2 = 0.69314718055994530942;
   double lrow = 0.0, lbreg = 0.0;
@@ -404,6 +408,10 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
       csum += mag_of(A, dtype, e);
     }
     if (csum + (double)(n - m) > 2.0e18) col_overflow = true;  // 2 * 2^62 headroom for the +-2 a updates
+  }
+  if (!glynn) {
+    if (!zero_row && lrow >= 126.5) *status = 3;
+    return;
   }
   if (zero_row) {
     if (col_overflow) *status = 3;
@@ -466,8 +474,8 @@ cudaError_t launch_glynn_gaussian(const SweepArgs& a, const LaunchCfg& c) {
 }
 
 cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
-                             cudaStream_t s) {
-  int_bound_kernel<<<1, 32, 0, s>>>(A, dtype, m, n, rs, cs, status);
+                             cudaStream_t s, bool glynn) {
+  int_bound_kernel<<<1, 32, 0, s>>>(A, dtype, m, n, rs, cs, status, glynn);
   return cudaGetLastError();
 }
 

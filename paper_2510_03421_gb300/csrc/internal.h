@@ -89,9 +89,10 @@ int glynn_int_blocks_per_sm(int n, int dtype, int block, bool grouped);
 cudaError_t launch_glynn_gaussian(const SweepArgs& a, const LaunchCfg& c);
 int glynn_gaussian_blocks_per_sm(int n, int block);
 int glynn_gaussian_max_n();
-// a-priori int128 range check; writes 3 (PERM_EOVERFLOW) to *status if exactness is not assured
+// a-priori int128 range check; writes 3 (PERM_EOVERFLOW) to *status if exactness is not
+// assured (glynn: for the Glynn / Ryser sums, else for the plain sum of products)
 cudaError_t launch_int_bound(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
-                             cudaStream_t s);
+                             cudaStream_t s, bool glynn = true);
 
 // --- Ryser over the 2^n column subsets in Gray-code order (ryser_f64.cu)
 // w[s] = (-1)^(m-s) C(n-s, m-s) for s <= m, else 0 (used when m < n)

@@ -1,5 +1,6 @@
 // Ryser's formula (Eq. ryser_square; Eq. ryser_rectangle in its subset-size form) for
-// complex input (FP64, Kahan-compensated) and for integer input (exact, modulo 2^128).
+// complex input (FP64, Kahan-compensated) and for integer and Gaussian-integer input
+// (exact, modulo 2^128).
 // Same walk as ryser_f64.cu: the 2^n column subsets in reflected Gray-code order,
 // subset(g) = set bits of gray(g), one column added or removed per step, the m row
 // sums updated by +-a_ic, and the term weighted by (-1)^(m-|S|) C(n-|S|, m-|S|).
@@ -185,6 +186,112 @@ __global__ void __launch_bounds__(256) ryser_int_kernel(SweepArgs a, IntWeights 
   }
 }
 
+// Gaussian integers (dtype 4): (re, im) row sums in int64, the product and the sums as
+// two 128-bit parts modulo 2^128.  Records: real parts at [0, grid), imaginary parts at
+// [grid, 2 grid), kIntRecord words each.
+template <int M>
+__global__ void __launch_bounds__(256) ryser_cint_kernel(SweepArgs a, IntWeights weights) {
+  extern __shared__ long long smem_i[];
+  __shared__ u128 scratch[2][32];
+  __shared__ u128 w[65];
+  const int n = a.n, m = a.m;
+  long long* sP = smem_i;  // sP[2 (c M + i)] = (re, im) of +a_ic
+  long long* sM = smem_i + 2 * n * M;
+  const long long* A = static_cast<const long long*>(a.A);
+  for (int idx = threadIdx.x; idx < n * M; idx += blockDim.x) {
+    const int c = idx / M, i = idx - c * M;
+    long long re = 0, im = 0;
+    if (i < m) {
+      const int64_t e = 2 * (i * a.rs + c * a.cs);
+      re = A[e];
+      im = A[e + 1];
+    }
+    sP[2 * idx] = re;
+    sP[2 * idx + 1] = im;
+    sM[2 * idx] = -re;
+    sM[2 * idx + 1] = -im;
+  }
+  for (int s = threadIdx.x; s <= n; s += blockDim.x) w[s] = ((u128)weights.hi[s] << 64) | weights.lo[s];
+  __syncthreads();
+
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t g, len;
+  split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
+  u128 acc_re = 0, acc_im = 0;
+  long long Rr[M], Ri[M];
+  int size = 0;
+  for (uint64_t s = 0; s < len; ++s, ++g) {
+    if (s == 0) {
+      const uint64_t gray = g ^ (g >> 1);
+      size = __popcll(gray);
+#pragma unroll
+      for (int i = 0; i < M; ++i) Rr[i] = Ri[i] = 0;
+      for (int c = 0; c < n; ++c) {
+        if (!((gray >> c) & 1u)) continue;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          Rr[i] += sP[2 * (c * M + i)];
+          Ri[i] += sP[2 * (c * M + i) + 1];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        if (i >= m) {
+          Rr[i] = 1;
+          Ri[i] = 0;
+        }
+    } else {
+      const int c = ctz64(g);
+      const bool added = !((g >> (c + 1)) & 1u);
+      size += added ? 1 : -1;
+      const long long* col = (added ? sP : sM) + 2 * c * M;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        Rr[i] += col[2 * i];
+        Ri[i] += col[2 * i + 1];
+      }
+    }
+    u128 pr = (u128)(__int128)Rr[0], pi = (u128)(__int128)Ri[0];
+#pragma unroll
+    for (int i = 1; i < M; ++i) {
+      const u128 xr = (u128)(__int128)Rr[i], xi = (u128)(__int128)Ri[i];
+      const u128 nr = pr * xr - pi * xi;
+      pi = pr * xi + pi * xr;
+      pr = nr;
+    }
+    acc_re += pr * w[size];
+    acc_im += pi * w[size];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    acc_re += shfl_down_u128(acc_re, off);
+    acc_im += shfl_down_u128(acc_im, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    scratch[0][warp] = acc_re;
+    scratch[1][warp] = acc_im;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    u128 xr = (lane < nw) ? scratch[0][lane] : (u128)0;
+    u128 xi = (lane < nw) ? scratch[1][lane] : (u128)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      xr += shfl_down_u128(xr, off);
+      xi += shfl_down_u128(xi, off);
+    }
+    if (lane == 0) {
+      unsigned long long* rec = static_cast<unsigned long long*>(a.partials);
+      rec[(size_t)blockIdx.x * kIntRecord] = (unsigned long long)xr;
+      rec[(size_t)blockIdx.x * kIntRecord + 1] = (unsigned long long)(xr >> 64);
+      rec[(size_t)(gridDim.x + blockIdx.x) * kIntRecord] = (unsigned long long)xi;
+      rec[(size_t)(gridDim.x + blockIdx.x) * kIntRecord + 1] = (unsigned long long)(xi >> 64);
+    }
+  }
+}
+
 template <int M>
 void* cplx_for(bool weighted) {
   return weighted ? (void*)ryser_c128_kernel<M, true> : (void*)ryser_c128_kernel<M, false>;
@@ -213,6 +320,19 @@ void* pick(int m, int dtype, bool weighted) {
       default: return nullptr;
     }
   }
+  if (dtype == 4) {
+    switch (M) {
+      case 4: return (void*)ryser_cint_kernel<4>;
+      case 8: return (void*)ryser_cint_kernel<8>;
+      case 12: return (void*)ryser_cint_kernel<12>;
+      case 16: return (void*)ryser_cint_kernel<16>;
+      case 20: return (void*)ryser_cint_kernel<20>;
+      case 24: return (void*)ryser_cint_kernel<24>;
+      case 28: return (void*)ryser_cint_kernel<28>;
+      case 32: return (void*)ryser_cint_kernel<32>;
+      default: return nullptr;
+    }
+  }
   switch (M) {
     case 4: return int_for<4>(dtype);
     case 8: return int_for<8>(dtype);
@@ -235,7 +355,7 @@ void* pick(int m, int dtype, bool weighted) {
 }
 
 size_t smem_bytes(int m, int n, int dtype) {
-  return 2u * (size_t)n * (size_t)((m + 3) & ~3) * (dtype == 1 ? 16 : 8);
+  return 2u * (size_t)n * (size_t)((m + 3) & ~3) * (dtype == 1 || dtype == 4 ? 16 : 8);
 }
 
 }  // namespace

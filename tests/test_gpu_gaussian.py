@@ -90,9 +90,6 @@ def test_overflow_and_refusals(capi, dev):
     out = np.zeros(4, dtype=np.int64)
     L = capi.lib()
     h = capi.handle(0)
-    for name in ("perm_ryser", "perm_combinatoric"):
-        rc = getattr(L, name)(h, G.ctypes.data, 4, 4, 4, capi.PERM_CI64, out.ctypes.data, None, None)
-        assert rc == capi.PERM_EUNSUPPORTED, name
     # perm_auto takes Glynn, the one algorithm for Gaussian integers: per(J_4 (1 + i)) = 24 (1 + i)^4
     assert L.perm_auto(h, G.ctypes.data, 4, 4, 4, capi.PERM_CI64, out.ctypes.data, None, None) == capi.PERM_OK
     assert capi.value(out, capi.PERM_CI64) == (-96, 0)
@@ -120,3 +117,36 @@ def test_gaussian_batch_exact_against_oracle(capi, dev):
     assert capi.value(out, capi.PERM_CI64, len(mats) - 1) == (math.factorial(16), 0)
     host = capi.perm_batched_gaussian(packed, offsets, M, N)
     assert all(capi.value(host, capi.PERM_CI64, b) == capi.value(out, capi.PERM_CI64, b) for b in range(len(mats)))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 3), (5, 5), (4, 7), (7, 4), (9, 9), (6, 12), (12, 12)])
+def test_gaussian_ryser_and_combinatoric_exact(capi, dev, m, n):
+    # Ryser's formula (size weights in int128, complex products modulo 2^128) and the
+    # combinatoric algorithm on Gaussian integers against the oracle in the same
+    # arithmetic; a third of the entries zero, so the combinatoric search prunes
+    g = inputs.rng(9980 + 13 * m + n)
+    keep = g.random((m, n)) < 0.67
+    re, im = g.integers(-3, 4, (m, n)) * keep, g.integers(-3, 4, (m, n)) * keep
+    G = np.ascontiguousarray(np.stack([re, im], -1).astype(np.int64))
+    want = oracle.glynn_gaussian(re, im)
+    for name in ("perm_ryser", "perm_combinatoric"):
+        if name == "perm_combinatoric" and max(m, n) > 9:
+            continue
+        out = np.zeros(4, dtype=np.int64)
+        rc = getattr(capi.lib(), name)(capi.handle(0), G.ctypes.data, m, n, n, capi.PERM_CI64, out.ctypes.data,
+                                       None, None)
+        assert rc == capi.PERM_OK, name
+        assert capi.value(out, capi.PERM_CI64) == want, name
+
+
+def test_integer_combinatoric_range_check(capi, dev):
+    # the combinatoric sum is exact while per(|A|) < 2^126.5: 6! (1e12)^6 is not
+    big = np.full((6, 6), 10 ** 12, dtype=np.int64)
+    out = np.zeros(2, dtype=np.int64)
+    rc = capi.lib().perm_combinatoric(capi.handle(0), big.ctypes.data, 6, 6, 6, capi.PERM_I64, out.ctypes.data, None,
+                                      None)
+    assert rc == capi.PERM_EOVERFLOW
+    ok = np.full((6, 6), 10 ** 5, dtype=np.int64)  # 6! 1e30 < 2^127
+    rc = capi.lib().perm_combinatoric(capi.handle(0), ok.ctypes.data, 6, 6, 6, capi.PERM_I64, out.ctypes.data, None,
+                                      None)
+    assert rc == capi.PERM_OK and capi.value(out, capi.PERM_I64) == 720 * 10 ** 30
