@@ -132,3 +132,17 @@ def test_cpp_interface_compiles_and_links(tmp_path):
     subprocess.check_call([gxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"),
                            os.path.join(ROOT, "tests", "paper_api_check.cpp"), lib, "-o", str(exe)])
     assert exe.exists()
+
+
+def test_public_headers_compile_cleanly():
+    # the C headers as C11 and the C++ interface as C++17, warnings as errors
+    import glob
+    import shutil
+    import subprocess
+    gcc, gxx = shutil.which("gcc"), shutil.which("g++")
+    if gcc is None or gxx is None:
+        pytest.skip("no gcc / g++")
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        subprocess.check_call([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", "c", h])
+    subprocess.check_call([gxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                           os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "paper_api_check.cpp")])
