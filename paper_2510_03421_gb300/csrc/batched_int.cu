@@ -16,6 +16,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "int_bound.cuh"
 #include "internal.h"
 
 namespace perm {
@@ -100,13 +101,13 @@ __global__ void __launch_bounds__(32 * kIntWarps) batched_int_kernel(BatchIntArg
         zero_row = true;
       } else {
         lrow = log2(rsum);
-        lbreg = lgamma(rsum + 1.0) / 0.69314718055994530942 / rsum;
+        lbreg = bregman_log2_term(rsum);
       }
     }
     if (lane < n) {
       double csum = 0.0;
       for (int i = 0; i < m; ++i) csum += fabs((double)entry(a.packed, a.dtype, base + i * rs + lane * cs));
-      col_over = csum + (double)(n - m) > 2.0e18;
+      col_over = column_sum_overflows(csum, m, n);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -181,15 +182,8 @@ __global__ void __launch_bounds__(32 * kIntWarps) batched_int_kernel(BatchIntArg
         lo = 1;
         hi = 0;
       } else {
-        // the bound of the single-matrix path
-        const double lfact = lgamma((double)(n - m) + 1.0) / 0.69314718055994530942;
-        double lb = (double)(n - 1) + lfact + lrow;
-        if (binary) {
-          const double lpad = (double)(n - m) * lgamma((double)n + 1.0) / 0.69314718055994530942 / (double)n;
-          const double lb2 = (double)(n - 1) + lbreg + lpad;
-          if (lb2 < lb) lb = lb2;
-        }
-        if (col_over || (!zero_row && lb >= 126.5)) atomicCAS(a.status, 0, 3);
+        if (col_over || (!zero_row && glynn_sum_log2_bound(m, n, lrow, lbreg, binary) >= kInt128Bits))
+          atomicCAS(a.status, 0, 3);
         // sum / 2^(n-1) / (n-m)!, exact divisions of the magnitude
         const bool negv = (int64_t)hi < 0;
         if (negv) {  // two's-complement negation
@@ -284,7 +278,7 @@ __global__ void __launch_bounds__(32 * kGaussWarps) batched_gauss_kernel(BatchIn
         const int64_t idx = base + i * rs + lane * cs;
         csum += fabs((double)P[2 * idx]) + fabs((double)P[2 * idx + 1]);
       }
-      col_over = csum + (double)(n - m) > 2.0e18;
+      col_over = column_sum_overflows(csum, m, n);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, off);
@@ -377,9 +371,8 @@ __global__ void __launch_bounds__(32 * kGaussWarps) batched_gauss_kernel(BatchIn
         rlo = 1;
         rhi = ilo = ihi = 0;
       } else {
-        const double lfact = lgamma((double)(n - m) + 1.0) / 0.69314718055994530942;
-        const double lb = (double)(n - 1) + lfact + lrow;
-        if (col_over || (!zero_row && lb >= 126.5)) atomicCAS(a.status, 0, 3);
+        if (col_over || (!zero_row && glynn_sum_log2_bound(m, n, lrow, 0.0, false) >= kInt128Bits))
+          atomicCAS(a.status, 0, 3);
         divide_exact(rlo, rhi, n - 1, n - m);
         divide_exact(ilo, ihi, n - 1, n - m);
       }

@@ -6,6 +6,7 @@
 // 2^(n-1) (n-m)! per(A) whenever that value fits in a signed 128-bit integer; the
 // a-priori bound kernel below flags inputs for which that is not guaranteed.
 #include "device_common.cuh"
+#include "int_bound.cuh"
 #include "internal.h"
 
 namespace perm {
@@ -384,7 +385,6 @@ __device__ __forceinline__ double mag_of(const void* A, int dtype, int64_t e) {
 __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t rs, int64_t cs, int* status,
                                  bool glynn) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double ln2 = 0.69314718055994530942;
   double lrow = 0.0, lbreg = 0.0;
   bool binary = true, zero_row = false, col_overflow = false;
   for (int i = 0; i < m; ++i) {
@@ -398,7 +398,7 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
     if (rsum == 0.0) zero_row = true;
     else {
       lrow += log2(rsum);
-      lbreg += lgamma(rsum + 1.0) / ln2 / rsum;
+      lbreg += bregman_log2_term(rsum);
     }
   }
   for (int j = 0; j < n; ++j) {
@@ -407,24 +407,17 @@ __global__ void int_bound_kernel(const void* A, int dtype, int m, int n, int64_t
       const int64_t e = i * rs + j * cs;
       csum += mag_of(A, dtype, e);
     }
-    if (csum + (double)(n - m) > 2.0e18) col_overflow = true;  // 2 * 2^62 headroom for the +-2 a updates
+    if (column_sum_overflows(csum, m, n)) col_overflow = true;
   }
   if (!glynn) {
-    if (!zero_row && lrow >= 126.5) *status = 3;
+    if (!zero_row && lrow >= kInt128Bits) *status = 3;
     return;
   }
   if (zero_row) {
     if (col_overflow) *status = 3;
     return;
   }
-  const double lfact = lgamma((double)(n - m) + 1.0) / ln2;
-  double lb = (double)(n - 1) + lfact + lrow;
-  if (binary) {
-    const double lpad = (double)(n - m) * lgamma((double)n + 1.0) / ln2 / (double)n;
-    const double lb2 = (double)(n - 1) + lbreg + lpad;
-    if (lb2 < lb) lb = lb2;
-  }
-  if (lb >= 126.5 || col_overflow) *status = 3;
+  if (glynn_sum_log2_bound(m, n, lrow, lbreg, binary) >= kInt128Bits || col_overflow) *status = 3;
 }
 
 }  // namespace
