@@ -165,8 +165,12 @@ int perm_batched(perm_handle h, const void* packed, const int64_t* offsets, cons
  * PERM_C128); n <= 32, N <= 64.  The columns are gathered inside the kernel; no
  * submatrix is materialised.  C, occ and out may each be device or host memory; out
  * receives `count` results (double, or (re, im) pairs).  A bitstring with the wrong
- * number of occupied states gets NaN.  FP64 arithmetic with compensated sums;
- * opts->chunk_log2 sets the rebuild interval of the column sums (default 14).
+ * number of occupied states gets NaN.  Real input runs on the integer pipes (exact
+ * fixed-point column sums, 64-bit-mantissa products, 192-bit sums; a column with a
+ * non-finite entry makes the bitstrings that occupy it NaN) unless opts->arith is
+ * PERM_ARITH_FP64; complex input, and real input with PERM_ARITH_FP64, use FP64 with
+ * compensated sums, opts->chunk_log2 setting the rebuild interval of the column sums
+ * (default 14).
  * Errors: PERM_EINVAL (shapes, null pointers), PERM_ETOOBIG (n > 32 or N > 64),
  * PERM_EUNSUPPORTED (integer dtypes). */
 int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int dtype, const uint64_t* occ,
