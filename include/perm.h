@@ -144,9 +144,9 @@ int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, in
  * (elements of `dtype`).  packed, offsets, M, N and out may each be device or host
  * memory; out receives `count` results laid out as for the single-matrix calls.
  * The call buckets the matrices by size and runs them in one persistent launch per
- * bucket, captured once into a CUDA graph and replayed for the same size signature.
- * Complex matrices of order >= 13 run on the integer pipes unless opts->arith is
- * PERM_ARITH_FP64; opts->exhaustive tunes the launch settings (and whether part of
+ * bucket, captured once into a CUDA graph and replayed for the same size signature;
+ * max(M[b], N[b]) <= 32.  Real and complex matrices of order >= 13 taken one per warp
+ * run on the integer pipes unless opts->arith is PERM_ARITH_FP64; opts->exhaustive tunes the launch settings (and whether part of
  * each product goes to the FP64 unit: forced on by PERM_ARITH_MIXED, off by
  * PERM_ARITH_FIXED) on a sample and keeps them for batches of the same sizes.
  * Integer matrices (PERM_U8, PERM_I64, PERM_CI64; max(M[b], N[b]) <= 32) are computed
