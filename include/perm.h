@@ -205,6 +205,18 @@ int perm_sbp(perm_handle h, const void* C, int64_t n, int64_t N, int64_t ld, int
 int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int64_t count, double* out,
                 void* stream, const perm_opts* opts);
 
+/* SBP coefficients (Eq. SBGpermanent) of a Cauchy coefficient matrix c_ij = 1/(x_i - y_j),
+ * i < n, j < N -- the form of the pairing wavefunctions the paper names as the source of
+ * Cauchy permanents: out[k] = per of the n x n Cauchy matrix of the points x and the y_j
+ * of the occupied states of occ[k] in increasing order (bit j set = state j occupied),
+ * by Borchardt's theorem as in perm_cauchy (opts->err as there).  x (n doubles), y (N),
+ * occ (count uint64) and out (count) may each be device or host memory.  A bitstring
+ * without exactly n occupied states below bit N gets NaN and status PERM_EINVAL, as
+ * coinciding points do (see perm_cauchy).  Errors: PERM_EINVAL (null pointers, n < 1,
+ * N < n, count < 0), PERM_ETOOBIG (n or N > 64), PERM_ENOMEM. */
+int perm_cauchy_sbp(perm_handle h, const double* x, int64_t n, const double* y, int64_t N, const uint64_t* occ,
+                    int64_t count, double* out, void* stream, const perm_opts* opts);
+
 /* Unnormalised partial Glynn sum over the terms g_begin <= g < g_end of Eq. glynn_rectangle:
  *     sum_g (-1)^g prod_j ( sum_{i<m} delta_i(g) a_ij + sum_{i>=m} delta_i(g) ),
  * where delta_i(g) = -1 if bit (n-1-i) of gray(g) = g ^ (g >> 1) is set, else +1,

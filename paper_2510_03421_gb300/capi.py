@@ -26,7 +26,8 @@ PERM_START_AUTO, PERM_START_SCALAR, PERM_START_DMMA = 0, 1, 2
 EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_combinatoric", "perm_auto",
            "perm_batched", "perm_glynn_partial", "perm_status_string", "perm_version", "perm_probe_rate", "perm_glynn_noalloc", "perm_device_status",
            "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
-           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp", "perm_cauchy")
+           "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp", "perm_cauchy",
+           "perm_cauchy_sbp")
 PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
 PERM_NCAND = 4
 PERM_CAND_CAUCHY = 8
@@ -69,6 +70,7 @@ def lib():
             L.perm_batched.argtypes = [vp, vp, vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_sbp.argtypes = [vp, vp, i64, i64, i64, i32, vp, i64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_cauchy.argtypes = [vp, vp, vp, i64, i64, vp, vp, ctypes.POINTER(perm_opts)]
+            L.perm_cauchy_sbp.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp, ctypes.POINTER(perm_opts)]
             L.perm_glynn_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, ctypes.c_int32]
             L.perm_device_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
             fp = ctypes.c_void_p
@@ -307,6 +309,23 @@ def perm_cauchy(x, y, out=None, stream=None, opts=None):
                            _stream(dev, stream), _opts(opts))
     if rc:
         raise PermError(rc, "perm_cauchy")
+    return out
+
+
+def perm_cauchy_sbp(x, y, occ, out=None, stream=None, opts=None):
+    """SBP coefficients of the Cauchy coefficient matrix 1 / (x_i - y_j): out[k] = per of
+    the Cauchy matrix of x and the y_j of the occupied states of occ[k] (uint64 bits)."""
+    dev = x.device if _is_torch(x) and x.is_cuda else None
+    if not _is_torch(x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+    count = len(occ)
+    if out is None:
+        out = _out_like(PERM_F64, dev, count)
+    rc = lib().perm_cauchy_sbp(handle(_device_index(dev)), _ptr(x), x.shape[-1], _ptr(y), y.shape[-1], _ptr(occ),
+                               count, _ptr(out), _stream(dev, stream), _opts(opts))
+    if rc:
+        raise PermError(rc, "perm_cauchy_sbp")
     return out
 
 

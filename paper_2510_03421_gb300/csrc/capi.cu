@@ -1404,4 +1404,82 @@ int perm_cauchy(perm_handle h, const double* x, const double* y, int64_t n, int6
   return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
 }
 
+int perm_cauchy_sbp(perm_handle h, const double* x, int64_t n, const double* y, int64_t N, const uint64_t* occ,
+                    int64_t count, double* out, void* stream, const perm_opts* opts) {
+  if (!h) return PERM_EINVAL;
+  if (count < 0 || n < 1 || N < n) return PERM_EINVAL;
+  if (count > 0 && (!x || !y || !occ || !out)) return PERM_EINVAL;
+  if (n > cauchy_max_n() || N > 64) return PERM_ETOOBIG;
+  if (count == 0) return PERM_OK;
+  if (cudaSetDevice(h->device) != cudaSuccess) return PERM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* err = opts ? opts->err : nullptr;
+  const bool hx = !on_device(x), hy = !on_device(y), hOcc = !on_device(occ), hOut = !on_device(out),
+             hErr = err && !on_device(err);
+  int block = 0;
+  const int grid = cauchy_grid(count, h->sms, &block);
+  const size_t scratch = align_up(8 * cauchy_scratch_words((int)n) * (size_t)grid);
+  const size_t state = align_up(cauchy_state_bytes(count));
+  const size_t pts = align_up(8 * (size_t)n * (size_t)count);
+  const size_t need = scratch + state + 2 * pts + (hx ? align_up(8 * (size_t)n) : 0) +
+                      (hy ? align_up(8 * (size_t)N) : 0) + (hOcc ? align_up(8 * (size_t)count) : 0) +
+                      (hOut ? align_up(8 * (size_t)count) : 0) + (hErr ? align_up(8 * (size_t)count) : 0);
+  int rc = ensure_sws(h, need);
+  if (rc) return rc;
+  if ((rc = ensure_ws(h, kWsDefault, s)) != PERM_OK) return rc;
+  char* base = static_cast<char*>(h->sws);
+  uint64_t* dScratch = reinterpret_cast<uint64_t*>(base);
+  base += scratch;
+  void* dState = base;
+  base += state;
+  double* xs = reinterpret_cast<double*>(base);
+  base += pts;
+  double* ys = reinterpret_cast<double*>(base);
+  base += pts;
+  const double* dx = x;
+  const double* dy = y;
+  const uint64_t* dOcc = occ;
+  double* dOut = out;
+  double* dErr = err;
+  if (hx) {
+    if (cudaMemcpyAsync(base, x, 8 * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dx = reinterpret_cast<const double*>(base);
+    base += align_up(8 * (size_t)n);
+  }
+  if (hy) {
+    if (cudaMemcpyAsync(base, y, 8 * (size_t)N, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dy = reinterpret_cast<const double*>(base);
+    base += align_up(8 * (size_t)N);
+  }
+  if (hOcc) {
+    if (cudaMemcpyAsync(base, occ, 8 * (size_t)count, cudaMemcpyHostToDevice, s) != cudaSuccess) return PERM_ECUDA;
+    dOcc = reinterpret_cast<const uint64_t*>(base);
+    base += align_up(8 * (size_t)count);
+  }
+  if (hOut) {
+    dOut = reinterpret_cast<double*>(base);
+    base += align_up(8 * (size_t)count);
+  }
+  if (hErr) dErr = reinterpret_cast<double*>(base);
+  const bool host_result = hOut || hErr;
+  int* st = host_result ? call_status_word(h) : status_word(h);
+  if (host_result && cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess) return PERM_ECUDA;
+  if (launch_cauchy_gather(dx, (int)n, dy, (int)N, dOcc, count, xs, ys, h->sms, s) != cudaSuccess ||
+      launch_cauchy(xs, ys, (int)n, count, dOut, dErr, dScratch, dState, grid, block, st, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (hOut && cudaMemcpyAsync(out, dOut, 8 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (hErr && cudaMemcpyAsync(err, dErr, 8 * (size_t)count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PERM_ECUDA;
+  if (host_result) {
+    int dev_status = 0;
+    if (cudaMemcpyAsync(&dev_status, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PERM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+    if (dev_status) return dev_status;
+  } else if (hx || hy || hOcc) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PERM_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? PERM_OK : PERM_ECUDA;
+}
+
 }  // extern "C"

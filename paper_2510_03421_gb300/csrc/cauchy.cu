@@ -111,6 +111,31 @@ __global__ void __launch_bounds__(kBlock) cauchy_fit_kernel(const double* __rest
   if (tid == 0) *ok = !s_bad;
 }
 
+// SBP coefficients of a Cauchy coefficient matrix c_ij = 1 / (x_i - y_j), i < n, j < N
+// (Eq. SBGpermanent with Cauchy structure): matrix k has the points x and the y_j of the
+// occupied states of occ[k] in increasing order.  A bitstring without exactly n states
+// below bit N gets NaN points (so the call marks it invalid).
+__global__ void cauchy_gather_kernel(const double* __restrict__ x, int n, const double* __restrict__ y, int N,
+                                     const uint64_t* __restrict__ occ, int64_t count, double* xs, double* ys) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint64_t below = N == 64 ? ~0ull : ((1ull << N) - 1);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+    const uint64_t bits = occ[k];
+    const bool ok = (bits & ~below) == 0 && __popcll(bits) == n;
+    uint64_t rest = bits;
+    for (int l = 0; l < n; ++l) {
+      xs[k * n + l] = x[l];
+      if (ok) {
+        const int j = __ffsll((long long)rest) - 1;
+        rest &= rest - 1;
+        ys[k * n + l] = y[j];
+      } else {
+        ys[k * n + l] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace cauchy
 
@@ -152,6 +177,15 @@ int cauchy_grid(int64_t count, int sms, int* block) {
   *block = kBlock;
   if (count < 1) return 1;
   return (int)(count < 2 * (int64_t)sms ? count : 2 * (int64_t)sms);
+}
+
+cudaError_t launch_cauchy_gather(const double* x, int n, const double* y, int N, const uint64_t* occ, int64_t count,
+                                 double* xs, double* ys, int sms, cudaStream_t stream) {
+  int64_t grid = (count + 255) / 256;
+  if (grid > 8 * (int64_t)sms) grid = 8 * (int64_t)sms;
+  if (grid < 1) grid = 1;
+  cauchy::cauchy_gather_kernel<<<(int)grid, 256, 0, stream>>>(x, n, y, N, occ, count, xs, ys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cauchy_fit(const double* A, int n, int64_t rs, int64_t cs, double tol, double* x, double* y,

@@ -185,6 +185,10 @@ int cauchy_grid(int64_t count, int sms, int* block);  // blocks (and threads per
 cudaError_t launch_cauchy(const double* x, const double* y, int n, int64_t count, double* out, double* err,
                           uint64_t* scratch, void* state, int grid, int block, int* status, cudaStream_t stream,
                           double rel_extra = 0.0);
+// the points of count Cauchy matrices from occupation bitstrings: xs[k n + l] = x[l],
+// ys[k n + l] = y[l-th occupied state of occ[k]] (NaN if occ[k] does not hold n states < N)
+cudaError_t launch_cauchy_gather(const double* x, int n, const double* y, int N, const uint64_t* occ, int64_t count,
+                                 double* xs, double* ys, int sms, cudaStream_t stream);
 // fit points x, y (n each, device) to a real n x n matrix (n <= 64); *ok = 1 if every
 // entry is 1 / (x_i - y_j) within relative tol, all of one sign (see cauchy.cu)
 cudaError_t launch_cauchy_fit(const double* A, int n, int64_t rs, int64_t cs, double tol, double* x, double* y,

@@ -146,3 +146,12 @@ def test_public_headers_compile_cleanly():
         subprocess.check_call([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-x", "c", h])
     subprocess.check_call([gxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
                            os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "paper_api_check.cpp")])
+
+
+def test_null_handle_cauchy_sbp(lib):
+    from paper_2510_03421_gb300 import capi
+    a = (ctypes.c_double * 4)()
+    occ = (ctypes.c_uint64 * 1)(3)
+    rc = lib.perm_cauchy_sbp(None, ctypes.addressof(a), 2, ctypes.addressof(a), 2, ctypes.addressof(occ), 1,
+                             ctypes.addressof(a), None, None)
+    assert rc == capi.PERM_EINVAL

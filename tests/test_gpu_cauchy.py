@@ -253,3 +253,49 @@ def test_vanishing_permanent_of_order_two(capi, dev):
     assert oracle.cauchy.permanent_definition(C) == 0
     got, err = gpu_cauchy(capi, dev, x, y, want_err=True)
     assert got[0] == 0.0 and err[0] == 0.0
+
+
+# --- SBP coefficients of a Cauchy coefficient matrix (perm_cauchy_sbp)
+
+
+def test_cauchy_sbp_matches_gathered_points_and_exact_values(capi, dev):
+    import torch
+    g = inputs.rng(2200)
+    n, N, count = 6, 14, 500
+    x = g.uniform(0.25, 0.75, n)        # rapidities
+    y = g.uniform(-0.75, -0.25, N)      # single-particle energies
+    cols = np.argsort(g.random((count, N)), axis=1)[:, :n]
+    occ = np.bitwise_or.reduce(np.left_shift(np.uint64(1), cols.astype(np.uint64)), axis=1)
+    out = capi.perm_cauchy_sbp(torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev),
+                               torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    ys = np.stack([y[[j for j in range(N) if (int(o) >> j) & 1]] for o in occ])
+    xs = np.tile(x, (count, 1))
+    ref = gpu_cauchy(capi, dev, xs, ys)
+    assert np.array_equal(got, ref)  # the same points through perm_cauchy: bit-identical
+    for k in range(0, count, 50):  # and exact: the oracle's C P (Eq. SBGpermanent) in rationals
+        assert within_ulp(got[k], exact(x, ys[k]))
+    host = capi.perm_cauchy_sbp(x, y, occ)
+    assert np.array_equal(host, got)
+
+
+def test_cauchy_sbp_bad_bitstrings_and_limits(capi, dev):
+    import torch
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    st = capi.ctypes.c_int(-1)
+    assert capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st)) == capi.PERM_OK
+    x = np.array([0.3, 0.6])
+    y = np.array([-0.3, -0.5, -0.7])
+    occ = np.array([0b011, 0b111, 0b1001, 0b110], dtype=np.uint64)  # 2nd: three states, 3rd: state 3 >= N
+    out = capi.perm_cauchy_sbp(torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev),
+                               torch.from_numpy(occ.view(np.int64)).to(dev))
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    assert np.isfinite(got[0]) and np.isnan(got[1]) and np.isnan(got[2]) and np.isfinite(got[3])
+    assert within_ulp(got[3], exact(x, y[[1, 2]]))
+    assert capi.lib().perm_device_status(capi.handle(0), stream, capi.ctypes.byref(st)) == capi.PERM_OK
+    assert st.value == capi.PERM_EINVAL
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_cauchy_sbp(x, np.zeros(65), np.array([3], dtype=np.uint64))
+    assert e.value.status == capi.PERM_ETOOBIG
