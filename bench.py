@@ -299,6 +299,38 @@ def run_sbp(args, dev, stream, count=1000000, n=12, N=24):
             "ms_per_call": ms}
 
 
+def run_batched_int(args, dev, stream):
+    """Exact batches: 100,000 0/1 matrices (Bernoulli(0.5)) and 100,000 Gaussian-integer
+    matrices (parts uniform in -2..2), n uniform in 4..20, one perm_batched call each
+    (one warp per matrix, int128)."""
+    import numpy as np
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    count = args.batch_count
+    g = inputs.rng(inputs.SEED_BASE + 8)
+    sizes = g.integers(4, 21, count).astype(np.int32)
+    offsets = np.zeros(count, np.int64)
+    offsets[1:] = np.cumsum(sizes.astype(np.int64) ** 2)[:-1]
+    total = int(offsets[-1] + int(sizes[-1]) ** 2)
+    res = {}
+    for kind, packed, fn in (("0/1", (g.random(total) < 0.5).astype(np.uint8), capi.perm_batched),
+                             ("gaussian", g.integers(-2, 3, 2 * total).astype(np.int64), capi.perm_batched_gaussian)):
+        tp, to, tM = (torch.from_numpy(a).to(dev) for a in (packed, offsets, sizes))
+        with torch.cuda.stream(stream):
+            out = fn(tp, to, tM, tM, stream=stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                fn(tp, to, tM, tM, out=out, stream=stream)
+                ev[k][1].record(stream)
+            stream.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        res[kind] = {"perms_per_s": count / (ms * 1e-3), "ms_per_batch": ms}
+    res["workload"] = "%d matrices per kind, n uniform in 4..20, seed %d; exact int128" % (count, inputs.SEED_BASE + 8)
+    return res
+
+
 def run_cauchy(args, dev, stream, count=1216, n=36):
     """Cauchy permanents by Borchardt's theorem (perm_cauchy): `count` matrices
     c_ij = 1 / (x_i - y_j) of order n with the points of the paper's accuracy tests
@@ -564,6 +596,7 @@ def run_ours(args):
         line["batched"]["frac_of_fp64_peak"] = line["batched"]["fp64_equiv_tflops"] * 1e12 / peak_flops
         line["batched_real"] = run_batched_real(args, dev, side)
         line["sbp"] = run_sbp(args, dev, side)
+        line["batched_int"] = run_batched_int(args, dev, side)
         line["cauchy"] = run_cauchy(args, dev, side)
         line["precision"] = run_precision(dev, side)
         line["other_configs"] = run_configs(dev, side)
