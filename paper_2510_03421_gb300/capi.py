@@ -2,10 +2,12 @@
 
 Argument marshalling only: every step of the computation runs in the CUDA
 library.  The functions keep the C names (``perm_glynn``, ``perm_ryser``,
-``perm_combinatoric``, ``perm_auto``, ``perm_batched``, ``perm_glynn_partial``)
-and accept torch tensors (CUDA or CPU) or numpy arrays; CPU / numpy buffers are
-passed as host pointers and the library copies them itself.  If the shared
-library has not been built this module raises -- there is no fallback.
+``perm_combinatoric``, ``perm_auto``, ``perm_batched``, ``perm_sbp``,
+``perm_cauchy``, ``perm_cauchy_sbp``, ``perm_glynn_partial``; Gaussian integers
+through ``perm_glynn_gaussian`` and ``perm_batched_gaussian``) and accept torch
+tensors (CUDA or CPU) or numpy arrays; CPU / numpy buffers are passed as host
+pointers and the library copies them itself.  If the shared library has not been
+built this module raises -- there is no fallback.
 """
 from __future__ import annotations
 
