@@ -529,3 +529,20 @@ def test_borchardt_small_closed_forms():
     assert oc.permanent_borchardt(x, y) == c[0][0] * c[1][1] + c[0][1] * c[1][0]
     with pytest.raises(ZeroDivisionError):
         oc.permanent_borchardt([0.5, 0.5], [-0.25, -0.5])
+
+
+def test_sbp_of_a_cauchy_matrix_equals_the_exact_cauchy_permanent():
+    # Eq. SBGpermanent with a Cauchy coefficient matrix: the oracle's C P permanent (long
+    # double, the selection matrix of the paper) against Borchardt's exact value for the
+    # occupied points -- two independent oracle paths
+    g = inputs.rng(760)
+    n, N = 5, 9
+    x = g.uniform(0.25, 0.75, n)
+    y = g.uniform(-0.75, -0.25, N)
+    C = 1.0 / (x[:, None] - y[None, :])
+    for occ in (0b000011111, 0b110101001, 0b101010101, 0b111110000):
+        ys = y[[j for j in range(N) if (occ >> j) & 1]]
+        want = float(oracle.cauchy.permanent_borchardt(x, ys))
+        got = oracle.sbp_coefficient(C, occ)
+        # C rounded to double (two roundings per entry, all terms positive): n 2u, plus the sum
+        assert abs(got - want) <= (2 * n + 4) * np.finfo(float).eps / 2 * want, (occ, got, want)
