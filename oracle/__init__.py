@@ -64,6 +64,9 @@ def _load():
                     getattr(lib, "oracle_ryser_square%s_%s" % (c, prec)).argtypes = [i, p, i64, p]
                     getattr(lib, "oracle_glynn_partial%s_%s" % (c, prec)).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_glynn_partial_abs_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_glynn_partial_abs_c_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_ryser_partial_abs_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
+                getattr(lib, "oracle_ryser_partial_abs_c_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_ryser_partial_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_glynn_rect_grouped_%s" % prec).argtypes = [i, i, p, i64, p]
                 getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec).argtypes = [i, i, p, i64, p]
@@ -181,17 +184,30 @@ def glynn_partial(A, g0: int, g1: int, prec: str = "ld", dd: bool = False):
 
 
 def glynn_partial_abs(A, g0: int, g1: int, prec: str = "ld") -> float:
-    """Sum of |term| over the Glynn terms g0 <= g < g1 (real input): the scale of the
-    rounding error of any evaluation of that partial sum."""
+    """Sum of |term| over the Glynn terms g0 <= g < g1 (real or complex input; complex
+    terms by their modulus): the scale of the rounding error of any evaluation of that
+    partial sum."""
     lib = _load()
     A, kind, m, n = _prepare(A)
-    if kind != "real":
-        raise TypeError("glynn_partial_abs takes a real matrix")
+    if kind == "int":
+        raise TypeError("glynn_partial_abs takes a real or complex matrix")
     if not (0 <= g0 <= g1 <= (1 << (n - 1))):
         raise ValueError("term range outside [0, 2^(n-1)]")
     out = (ctypes.c_double * 2)()
-    getattr(lib, "oracle_glynn_partial_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
+    fn = "oracle_glynn_partial_abs_%s%s" % ("c_" if kind == "complex" else "", prec)
+    getattr(lib, fn)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
     return float(out[0]) + float(out[1])
+
+
+def glynn_abs(A, prec: str = "ld") -> float:
+    """Sum of |term| over all 2^(n-1) terms of Eq. glynn_rectangle divided by the
+    normalisation 2^(n-1) (n-m)!: the size, in units of per(A), of the terms Glynn's
+    formula cancels (real or complex input; 1 for an empty matrix)."""
+    A_, kind, m, n = _prepare(A)
+    if m == 0:
+        return 1.0
+    s = glynn_partial_abs(A_, 0, 1 << (n - 1), prec)
+    return s / (2.0 ** (n - 1)) / float(np.prod(np.arange(1, n - m + 1, dtype=np.float64)))
 
 
 def glynn_rect_grouped(A, prec: str = "ld", dd: bool = False):
@@ -229,6 +245,42 @@ def ryser_partial(A, g0: int, g1: int, prec: str = "ld") -> float:
     out = (ctypes.c_double * 2)()
     getattr(lib, "oracle_ryser_partial_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
     return float(out[0]) + float(out[1])
+
+
+def ryser_partial_abs(A, g0: int, g1: int, prec: str = "ld") -> float:
+    """Sum of |weight * prod_i rowsum_i| over the Gray-ordered column subsets g0 <= g < g1
+    (the terms of ryser_partial; real or complex input, complex by modulus)."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind == "int":
+        raise TypeError("ryser_partial_abs takes a real or complex matrix")
+    if not (0 <= g0 <= g1 <= (1 << n)):
+        raise ValueError("subset range outside [0, 2^n]")
+    out = (ctypes.c_double * 2)()
+    fn = "oracle_ryser_partial_abs_%s%s" % ("c_" if kind == "complex" else "", prec)
+    getattr(lib, fn)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, g0, g1, out)
+    return float(out[0]) + float(out[1])
+
+
+def ryser_abs(A, prec: str = "ld") -> float:
+    """Sum of |term| over all terms of Ryser's formula (Eq. ryser_square; for m < n the
+    subset-size form of Eq. ryser_rectangle with weights C(n-s, m-s)): the size of the
+    terms Ryser's sum cancels (real or complex input; 1 for an empty matrix)."""
+    A_, kind, m, n = _prepare(A)
+    if m == 0:
+        return 1.0
+    return ryser_partial_abs(A_, 0, 1 << n, prec)
+
+
+def definition_abs(A, prec: str = "ld") -> float:
+    """Sum of |term| over the terms of the definition (Eq.
+    rectangular_permanent_definition), i.e. per(|A|) with |A| the entrywise modulus;
+    every term of per(|A|) is nonnegative, so Glynn's sum of |A| evaluates it with
+    little cancellation."""
+    A = np.abs(np.asarray(A)).astype(np.float64)
+    if min(A.shape) == 0:
+        return 1.0
+    return float(glynn(A, prec))
 
 
 def ryser_square(A, prec: str = "ld", dd: bool = False):

@@ -35,6 +35,7 @@
  */
 #include <complex.h>
 #include <float.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -93,15 +94,19 @@ static int next_combination(int* comb, int s, int n) {
 
 #define REAL long double
 #define SFX(name) name##_ld
+#define SQRT_REAL sqrtl
 #include "oracle_real.inc"
 #undef REAL
 #undef SFX
+#undef SQRT_REAL
 
 #define REAL double
 #define SFX(name) name##_f64
+#define SQRT_REAL sqrt
 #include "oracle_real.inc"
 #undef REAL
 #undef SFX
+#undef SQRT_REAL
 
 /* ===========================================================================
  * Exact integer versions.  Input: int64 entries, row-major with ld.  Output:

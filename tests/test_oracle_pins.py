@@ -546,3 +546,109 @@ def test_sbp_of_a_cauchy_matrix_equals_the_exact_cauchy_permanent():
         got = oracle.sbp_coefficient(C, occ)
         # C rounded to double (two roundings per entry, all terms positive): n 2u, plus the sum
         assert abs(got - want) <= (2 * n + 4) * np.finfo(float).eps / 2 * want, (occ, got, want)
+
+
+# ---------------------------------------------------------------------------
+# Sums of |term| (the scales every float tolerance of the GPU tests is built on),
+# pinned to closed forms that do not go through the oracle's term loops.
+#
+# Glynn on the all-ones m x n matrix (padded with rows of ones, Eq. glynn_rectangle):
+# every column sum equals n - 2t, t = number of -1 signs among the n - 1 free rows,
+# so sum|t| = sum_t C(n-1, t) |n - 2t|^n.  Scaling column j by v_j scales every term
+# by v_j.  A diagonal matrix has |term| = prod_j |d_j| for each of the 2^(n-1) terms.
+# Ryser on the all-ones m x n matrix: every row sum over S equals |S| = s, so
+# sum|t| = sum_{s=1..m} C(n, s) C(n-s, m-s) s^m; scaling row i by r_i scales every
+# term by r_i; a diagonal matrix has one nonzero term, the full set, prod_i |d_i|.
+
+def _glynn_ones_abs(n):
+    return sum(math.comb(n - 1, t) * abs(n - 2 * t) ** n for t in range(n))
+
+
+def _ryser_ones_abs(m, n):
+    return sum(math.comb(n, s) * math.comb(n - s, m - s) * s ** m for s in range(1, m + 1))
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 13])
+def test_glynn_abs_all_ones_and_column_scaling(n):
+    v = inputs.rng(600 + n).uniform(-2, 2, n)
+    exact = _glynn_ones_abs(n) * float(np.prod(np.abs(v)))
+    A = np.ones((n, n)) * v[None, :]
+    assert _rel(oracle.glynn_partial_abs(A, 0, 1 << (n - 1)), exact) < 1e-15
+    Ac = A * np.exp(1j * inputs.rng(610 + n).uniform(0, 6.3, n))[None, :]
+    assert _rel(oracle.glynn_partial_abs(Ac, 0, 1 << (n - 1)), exact) < 1e-15
+    assert _rel(oracle.glynn_abs(A), exact / 2.0 ** (n - 1)) < 1e-15
+
+
+@pytest.mark.parametrize("m,n", [(1, 4), (2, 7), (3, 8), (5, 11), (4, 30), (2, 60)])
+def test_glynn_abs_all_ones_rectangle(m, n):
+    exact = float(_glynn_ones_abs(n))
+    A = np.ones((m, n))
+    assert _rel(oracle.glynn_rect_grouped_abs(A), exact) < 1e-15
+    if n <= 14:
+        assert _rel(oracle.glynn_partial_abs(A, 0, 1 << (n - 1)), exact) < 1e-15
+        assert _rel(oracle.glynn_partial_abs(A.astype(complex), 0, 1 << (n - 1)), exact) < 1e-15
+        norm = 2.0 ** (n - 1) * math.factorial(n - m)
+        assert _rel(oracle.glynn_abs(A), exact / norm) < 1e-15
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 10])
+def test_glynn_abs_diagonal(n):
+    d = inputs.rng(620 + n).uniform(0.5, 2, n) * np.where(np.arange(n) % 2, -1, 1)
+    exact = 2.0 ** (n - 1) * float(np.prod(np.abs(d)))
+    assert _rel(oracle.glynn_partial_abs(np.diag(d), 0, 1 << (n - 1)), exact) < 1e-15
+    assert _rel(oracle.glynn_rect_grouped_abs(np.diag(d)), exact) < 1e-15
+    dc = d * np.exp(1j * np.arange(n))
+    assert _rel(oracle.glynn_partial_abs(np.diag(dc), 0, 1 << (n - 1)), exact) < 1e-15
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 3), (4, 9), (6, 6), (5, 12)])
+def test_ryser_abs_all_ones_row_scaling_and_diagonal(m, n):
+    r = inputs.rng(630 + m + n).uniform(-2, 2, m)
+    exact = _ryser_ones_abs(m, n) * float(np.prod(np.abs(r)))
+    A = r[:, None] * np.ones((m, n))
+    assert _rel(oracle.ryser_abs(A), exact) < 1e-15
+    Ac = A * np.exp(1j * inputs.rng(640 + m).uniform(0, 6.3, m))[:, None]
+    assert _rel(oracle.ryser_abs(Ac), exact) < 1e-15
+    d = np.abs(r) + 0.25
+    assert _rel(oracle.ryser_abs(np.diag(d)), float(np.prod(d))) < 1e-15
+
+
+@pytest.mark.parametrize("m,n,kind", [(5, 5, "real"), (4, 8, "real"), (5, 5, "complex"), (3, 7, "complex")])
+def test_abs_sums_are_invariant_and_split_over_ranges(m, n, kind):
+    # sum|t| of Glynn and of Ryser is unchanged by row and column permutations (Glynn:
+    # flipping every sign leaves |term| unchanged, so the fixed first sign is no
+    # restriction), scales by |c| with a column (square Glynn) or row (Ryser) scaled by
+    # c, and partial ranges add up to the whole.
+    g = inputs.rng(650 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    if kind == "complex":
+        A = A + 1j * g.uniform(-1, 1, (m, n))
+    ga, ra = oracle.glynn_abs(A), oracle.ryser_abs(A)
+    P = A[g.permutation(m)][:, g.permutation(n)]
+    assert _rel(oracle.glynn_abs(P), ga) < 1e-14
+    assert _rel(oracle.ryser_abs(P), ra) < 1e-14
+    c = 1.75 if kind == "real" else 1.0 - 1.5j
+    if m == n:  # (the padding rows of a rectangle are not scaled with a column)
+        B = A.copy()
+        B[:, 1] *= c
+        assert _rel(oracle.glynn_abs(B), abs(c) * ga) < 1e-14
+    B = A.copy()
+    B[1, :] *= c
+    assert _rel(oracle.ryser_abs(B), abs(c) * ra) < 1e-14
+    h = 1 << (n - 2)
+    whole = oracle.glynn_partial_abs(A, 0, 1 << (n - 1))
+    assert _rel(oracle.glynn_partial_abs(A, 0, h) + oracle.glynn_partial_abs(A, h, 1 << (n - 1)), whole) < 1e-15
+    assert _rel(oracle.ryser_partial_abs(A, 0, 5) + oracle.ryser_partial_abs(A, 5, 1 << n), ra) < 1e-15
+    # each sum|t| bounds the modulus of its (normalised) sum
+    assert abs(oracle.glynn(A)) <= ga * (1 + 1e-14)
+    assert abs(oracle.ryser(A)) <= ra * (1 + 1e-14)
+
+
+@pytest.mark.parametrize("m,n", [(3, 3), (4, 6), (5, 5)])
+def test_definition_abs_is_permanent_of_moduli(m, n):
+    # per(|A|) by brute force over the injective maps; ones give n!/(n-m)!
+    g = inputs.rng(670 + m + n)
+    A = g.uniform(-1, 1, (m, n)) + 1j * g.uniform(-1, 1, (m, n))
+    brute = sum(float(np.prod([abs(A[i, s[i]]) for i in range(m)])) for s in itertools.permutations(range(n), m))
+    assert _rel(oracle.definition_abs(A), brute) < 1e-14
+    assert oracle.definition_abs(np.ones((m, n))) == pytest.approx(math.factorial(n) / math.factorial(n - m), rel=1e-15)
