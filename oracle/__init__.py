@@ -70,6 +70,9 @@ def _load():
                 getattr(lib, "oracle_ryser_partial_%s" % prec).argtypes = [i, i, p, i64, u64, u64, p]
                 getattr(lib, "oracle_glynn_rect_grouped_%s" % prec).argtypes = [i, i, p, i64, p]
                 getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec).argtypes = [i, i, p, i64, p]
+                getattr(lib, "oracle_glynn_esym_abs_%s" % prec).argtypes = [i, i, p, i64, p]
+                getattr(lib, "oracle_glynn_esym_abs_c_%s" % prec).argtypes = [i, i, p, i64, p]
+                getattr(lib, "oracle_ryser_rect_abs_%s" % prec).argtypes = [i, i, p, i64, p]
             for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
             lib.oracle_ryser_square_i128.argtypes = [i, p, i64, p]
@@ -234,6 +237,23 @@ def glynn_rect_grouped_abs(A, prec: str = "ld") -> float:
     return float(out[0]) + float(out[1])
 
 
+def glynn_esym_abs(A, prec: str = "ld") -> float:
+    """Scale of the rounding error of Eq. glynn_rectangle with the padding summed in
+    closed form, per(A) = 2^-(m-1) sum_delta (prod delta) e_m(c(delta)): the sum over
+    the 2^(m-1) sign vectors of e_m(|c|), divided by 2^(m-1) (real or complex input,
+    |c| the modulus; equals glynn_abs for a square matrix)."""
+    lib = _load()
+    A, kind, m, n = _prepare(A)
+    if kind == "int":
+        raise TypeError("glynn_esym_abs takes a real or complex matrix")
+    if m == 0:
+        return 1.0
+    out = (ctypes.c_double * 2)()
+    fn = "oracle_glynn_esym_abs_%s%s" % ("c_" if kind == "complex" else "", prec)
+    getattr(lib, fn)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, out)
+    return (float(out[0]) + float(out[1])) / 2.0 ** (m - 1)
+
+
 def ryser_partial(A, g0: int, g1: int, prec: str = "ld") -> float:
     """Weighted Ryser sum over the Gray-ordered column subsets g0 <= g < g1 (real input)."""
     lib = _load()
@@ -269,6 +289,11 @@ def ryser_abs(A, prec: str = "ld") -> float:
     A_, kind, m, n = _prepare(A)
     if m == 0:
         return 1.0
+    if kind == "real" and m < n:
+        # by subset size (combinations), as the rectangular appendix algorithm visits them
+        out = (ctypes.c_double * 2)()
+        getattr(_load(), "oracle_ryser_rect_abs_%s" % prec)(m, n, A_.ctypes.data_as(ctypes.c_void_p), n, out)
+        return float(out[0]) + float(out[1])
     return ryser_partial_abs(A_, 0, 1 << n, prec)
 
 

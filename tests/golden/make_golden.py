@@ -9,6 +9,7 @@ Every value here comes from the CPU oracle (``oracle/``) alone, on inputs drawn 
 import os
 import sys
 import time
+from fractions import Fraction
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
@@ -68,15 +69,30 @@ def rect20x40_f64():
     norm = 2.0 ** (n - 1) * float(np.prod(np.arange(1, n - m + 1, dtype=np.float64)))
     bound = (n + 4 + 2.0 ** (m - 1) * (n - m + 1)) * 2.0 ** -53 * s / norm
     assert abs(g64 - (g[0] + g[1])) <= bound, (g64, g, bound)
+    # the same grouped sum in exact integers (oracle.exact): the long-double value
+    # above is limited by its own rounding of a sum that cancels 10^7-fold
+    from oracle import exact
+    t2 = time.time()
+    ex = exact.glynn_rect_grouped(A, workers=os.cpu_count() or 1)
+    t3 = time.time()
+    exd = float(ex)
+    exlo = float(ex - Fraction(exd))
+    assert abs(exd - (g[0] + g[1])) <= (n + 4) * 2.0 ** -(oracle.ldbl_mant_dig() - 1) * s / norm
+    esym = oracle.glynn_esym_abs(A)
     write("rect20x40_f64.txt", [
         "# 20 x 40 float64 uniform[0,1] from inputs.rect20x40_f64() (seed %d)." % (inputs.SEED_BASE + 3),
         "# Oracle Glynn with the 20 padding rows grouped by their number of -1 signs (Eq. glynn_rectangle),",
         "# long double (LDBL_MANT_DIG = %d), %.1f s; as double-double hi lo.  sum_abs is the sum of |term|" % (
             oracle.ldbl_mant_dig(), t1 - t0),
         "# over all 2^39 terms, unnormalised (the scale of any evaluation's rounding error).",
+        "# exact: the same sum in exact integers (oracle.exact, %.0f s), rounded to a double-double hi lo." % (t3 - t2),
+        "# esym_abs: sum over the 2^19 real-row sign vectors of e_20(|c|) / 2^19, the scale of the closed-form",
+        "# padding sum (oracle.glynn_esym_abs).",
         "seed %d" % (inputs.SEED_BASE + 3),
         "glynn %r %r" % g,
         "sum_abs %r" % s,
+        "exact %r %r" % (exd, exlo),
+        "esym_abs %r" % esym,
     ])
 
 
@@ -104,6 +120,9 @@ def cauchy_exact():
 if __name__ == "__main__":
     if sys.argv[1:] == ["cauchy"]:
         cauchy_exact()
+        sys.exit(0)
+    if sys.argv[1:] == ["rect"]:
+        rect20x40_f64()
         sys.exit(0)
     square16_f64()
     square26_01()

@@ -652,3 +652,63 @@ def test_definition_abs_is_permanent_of_moduli(m, n):
     brute = sum(float(np.prod([abs(A[i, s[i]]) for i in range(m)])) for s in itertools.permutations(range(n), m))
     assert _rel(oracle.definition_abs(A), brute) < 1e-14
     assert oracle.definition_abs(np.ones((m, n))) == pytest.approx(math.factorial(n) / math.factorial(n - m), rel=1e-15)
+
+
+# Scale of the closed-form padding sum: sum over the 2^(m-1) sign vectors of
+# e_m(|c|) / 2^(m-1).  All-ones m x n: every column sum is m - 2t, so it is
+# C(n, m) sum_t C(m-1, t) |m - 2t|^m / 2^(m-1); [D | 0] with D diagonal: only the
+# first m columns are nonzero and e_m(|c|) = prod |d_j| for every sign vector; a
+# square matrix gives Glynn's own sum of |term|.
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 6), (3, 3), (3, 9), (5, 11), (8, 20)])
+def test_esym_abs_closed_forms(m, n):
+    exact = math.comb(n, m) * sum(math.comb(m - 1, t) * abs(m - 2 * t) ** m for t in range(m)) / 2.0 ** (m - 1)
+    assert _rel(oracle.glynn_esym_abs(np.ones((m, n))), exact) < 1e-15
+    d = inputs.rng(700 + m + n).uniform(0.5, 2, m) * np.where(np.arange(m) % 2, -1, 1)
+    Z = np.zeros((m, n))
+    Z[np.arange(m), np.arange(m)] = d
+    assert _rel(oracle.glynn_esym_abs(Z), float(np.prod(np.abs(d)))) < 1e-15
+    ph = np.exp(1j * inputs.rng(705 + m).uniform(0, 6.3, m))
+    assert _rel(oracle.glynn_esym_abs(Z * ph[:, None]), float(np.prod(np.abs(d)))) < 1e-15
+    assert _rel(oracle.glynn_esym_abs(np.ones((m, n), complex)), exact) < 1e-15
+    if m == n:
+        A = inputs.rng(710 + n).uniform(-1, 1, (n, n))
+        assert _rel(oracle.glynn_esym_abs(A), oracle.glynn_abs(A)) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(3, 7), (5, 9)])
+def test_esym_abs_invariants_and_bound(m, n):
+    # unchanged by row and column permutations, scaled by |c|^m with the matrix scaled
+    # by c (every product in e_m has m factors), and it bounds |per(A)|
+    g = inputs.rng(720 + m + n)
+    A = g.uniform(-1, 1, (m, n))
+    s = oracle.glynn_esym_abs(A)
+    P = A[g.permutation(m)][:, g.permutation(n)]
+    assert _rel(oracle.glynn_esym_abs(P), s) < 1e-14
+    assert _rel(oracle.glynn_esym_abs(-2.5 * A), 2.5 ** m * s) < 1e-14
+    assert abs(oracle.glynn(A)) <= s * (1 + 1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Exact integer evaluation (oracle.exact): the definition on tiny inputs, closed forms
+# and the long-double grouped sum on a well-conditioned shape.
+def test_exact_grouped_glynn_pins():
+    from oracle import exact
+    for (m, n) in [(1, 3), (2, 5), (3, 6), (4, 4)]:
+        A = inputs.rng(800 + m + n).uniform(-1, 1, (m, n))
+        assert exact.glynn_rect_grouped(A) == exact.definition(A)
+        assert exact.glynn_rect_grouped(A.T) == exact.definition(A)
+    assert exact.glynn_rect_grouped(np.ones((3, 9))) == math.factorial(9) // math.factorial(6)
+    assert exact.glynn_rect_grouped(np.eye(5)[:3]) == 1
+    A = inputs.rng(811).uniform(0, 1, (6, 10))
+    assert _rel(float(exact.glynn_rect_grouped(A)), oracle.glynn_rect_grouped(A)) < 1e-15
+    Z, s = exact.to_integer_matrix(np.array([[0.5, -0.25], [3.0, 2.0 ** -40]]))
+    assert s == 40 and Z[0][0] == 2 ** 39 and Z[1][1] == 1 and Z[0][1] == -(2 ** 38)
+
+
+@pytest.mark.parametrize("m,n", [(2, 5), (3, 8), (5, 9)])
+def test_ryser_abs_by_size_equals_gray_enumeration(m, n):
+    # the combination enumeration and the Gray-ordered enumeration visit the same
+    # weighted subsets (all-ones closed form pinned above)
+    A = inputs.rng(740 + m + n).uniform(-1, 1, (m, n))
+    assert _rel(oracle.ryser_abs(A), oracle.ryser_partial_abs(A, 0, 1 << n)) < 1e-14
+    assert _rel(oracle.ryser_abs(np.ones((m, n))), _ryser_ones_abs(m, n)) < 1e-15
