@@ -240,17 +240,21 @@ int perm_ryser_partial(perm_handle h, const void* A, int64_t m, int64_t n, int64
  * as runtimes that hand out every buffer from a pool reserved up front or plugin
  * hosts that forbid cudaMalloc.  The paper has no counterpart; this is a deployment
  * variant of perm_glynn.
- *   A, out   device (or managed) pointers on the current device; host pointers are
- *            rejected with PERM_EINVAL.  Layout as for perm_glynn; out gets 1 double.
+ *   A, out   device (or managed) pointers on the current device; host pointers and
+ *            another device's memory are rejected with PERM_EINVAL before anything is
+ *            launched.  Layout as for perm_glynn; out gets 1 double.
  *   grid     blocks of the sweep, 0 = chosen by the library; at most 2048, larger
  *            values return PERM_ETOOBIG.
  * The call allocates nothing: its scratch (2048 records of 32 bytes, 64 KiB) is a
  * fixed array in device memory that the library declares, present on every GPU
  * that loads the library until the process exits.  The first call on a device looks
  * up that array's device address; make that first call before any stream capture.
+ * The address is kept for the life of the process: after cudaDeviceReset on a device
+ * (which discards the array with the context) do not call this function again.
  * Every call shares the array, so calls whose kernels overlap on a GPU (for
  * example on two streams) race and must be serialised by the caller.  No part of the
- * scratch needs to start at zero.  No error bound is produced. */
+ * scratch needs to start at zero.  No error bound is produced.  PERM_ECUDA if the
+ * sweep's launch configuration cannot be set up on this device. */
 int perm_glynn_noalloc(const void* A, int64_t m, int64_t n, int64_t ld, void* out, void* stream, int32_t grid);
 
 /* Device-detected status since the last call of this function on handle h:

@@ -234,7 +234,7 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   const bool want_abs = c.dErr != nullptr;
   const int block = 256;
   int bps = glynn_f64_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kRealRecord * sizeof(double));
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, (want_abs ? kCplxRecord : kRealRecord) * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a;
   a.A = c.dA;
@@ -248,22 +248,66 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   a.start_mode = c.o.start ? c.o.start : PERM_START_SCALAR;
   a.partials = partials_base(c.h);
   if (launch_glynn_f64(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
-  // error bound: products (n-1 roundings), the Kahan sum (2), and the drift of the
-  // column sums over at most 2^chunk_log2 incremental updates (n columns)
+  // error bound: products (n-1 roundings) and the Kahan sum (2) against sum |term|; the
+  // column sums' own errors (rebuild and drift, bounded by the columns' absolute sums)
+  // through the per-term widened products; their FP64 evaluation (2 (n-1) u)
   const double u = 1.1102230246251565e-16;
-  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
-  const double coef = u * ((double)c.n + 4.0 + 2.0 * (double)c.n * L);
-  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
-                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
-    return PERM_ECUDA;
+  const double coef = u * ((double)c.n + 4.0);
+  const cudaError_t f =
+      want_abs ? launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                                     static_cast<double*>(c.dOut), c.dErr, raw, c.stream, 2.0 * u * (c.n + 1))
+               : launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                                    static_cast<double*>(c.dOut), nullptr, raw, c.stream);
+  if (f != cudaSuccess) return PERM_ECUDA;
   return PERM_OK;
 }
 
+
+// Rectangular real Glynn with the padding rows summed in closed form (glynn_esym.cu):
+// per(A) = 2^-(m-1) sum_d (prod d) e_m(c(d)).  Taken for m <= 32 when n - m >= 3 (or
+// m <= 8): there the padded walk cancels far more (10^3 .. 10^16 times |per| on
+// uniform entries) and e_m costs m n software multiply-adds per sign vector against
+// (n - m + 1) n for the padded products.
+bool use_esym(const Call& c) {
+  return c.m < c.n && c.m <= glynn_esym_max_m() && (c.n - c.m >= 3 || c.m <= 8);
+}
+
+int glynn_esym_run(Call& c) {
+  const bool want_abs = c.dErr != nullptr;
+  const int block = glynn_esym_block();
+  if (c.o.block > block) return PERM_EINVAL;
+  const int nb = c.o.block ? c.o.block : block;
+  const uint64_t g1 = 1ull << (c.m - 1);
+  const int bps = glynn_esym_blocks_per_sm(c.m, c.n, nb, want_abs);
+  if (bps <= 0) return PERM_ECUDA;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1, 1, kCplxRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, g1, 0);
+  if (!c.o.chunk_log2) {
+    // chunks of 2^k sign vectors, four rounds of 32 chunks per resident warp if there are enough
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 12;
+    while (k > 0 && (g1 >> k) < 128 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  static_assert(sizeof(EsymTable) <= kPartialsOffset - kFxTableOffset, "e_m table slot");
+  EsymTable* tab = reinterpret_cast<EsymTable*>(fx_table(c.h));
+  if (launch_glynn_esym(a, tab, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // each product of the recurrence truncates by < 2^-60, each sum by < 2^-60 of the
+  // larger operand: relative to e_m(|c|), m + n roundings; 4 more for the
+  // accumulator window, the double-double reduction and the sums of the bound itself
+  const double coef = std::ldexp((double)(c.m + c.n) + 4.0, -60);
+  if (launch_esym_finish(static_cast<const double*>(a.partials), lc.grid, c.m, coef, static_cast<double*>(c.dOut),
+                         c.dErr, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
 
 // Real Glynn on the integer pipes: exact fixed-point column sums, 64-bit-mantissa
 // products, 192-bit accumulation (glynn_fx.cu).
 int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
   const bool want_abs = c.dErr != nullptr;
+  if (!raw && use_esym(c)) return glynn_esym_run(c);
   // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
   const bool grouped = !raw && c.m < c.n;
   // 6 warps, two blocks per SM at up to 168 registers (square kernel from N = 40: 4 warps)
@@ -276,7 +320,9 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
   const int bps = grouped ? glynn_fxg_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block)
                           : glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, mixed);
   const uint64_t work = grouped ? (g1 - g0) * (uint64_t)(c.n - c.m + 1) : g1 - g0;
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, work, 16, kRealRecord * sizeof(double));
+  // with an error bound both sweeps write {sum, sum |term|, eta-widened sum}
+  const bool three = want_abs;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, work, 16, (three ? kCplxRecord : kRealRecord) * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 12);
   if (!c.o.chunk_log2) {
@@ -293,14 +339,17 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
                                 : launch_glynn_fx(a, fx_table(c.h), lc, want_abs, mixed);
   if (e != cudaSuccess) return PERM_ECUDA;
   // relative error of a term against |term|: n/2 pair products of < 2^-59 each (the
-  // running mantissa keeps >= 60 bits), the quantisation of A (< 2^-62 of each
-  // column's absolute sum), the binomial weight of a grouped term (< 2^-62); the
-  // mixed variant's K columns: K conversions and K - 1 multiplications in FP64
+  // running mantissa keeps >= 60 bits), the binomial weight of a grouped term (< 2^-62);
+  // the mixed variant's K columns: K conversions and K - 1 multiplications in FP64.
+  // The bound variants take exact magnitudes and bound the rounding of A to fixed
+  // point by their eta-widened products (zero when every entry was exact)
   const int K = (mixed && !grouped) ? glynn_fx_mixed_columns(c.n) : 0;
   const double coef = std::ldexp((double)(c.n - K) + 5.0, -60) + std::ldexp(2.0 * K, -53);
-  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
-                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
-    return PERM_ECUDA;
+  const cudaError_t f = three ? launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
+                                                    coef, static_cast<double*>(c.dOut), c.dErr, raw, c.stream)
+                              : launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
+                                                   coef, static_cast<double*>(c.dOut), c.dErr, raw, c.stream);
+  if (f != cudaSuccess) return PERM_ECUDA;
   return PERM_OK;
 }
 
@@ -342,9 +391,39 @@ SweepArgs sweep_args(const Call& c, uint64_t g0, uint64_t g1, int default_chunk)
   return a;
 }
 
+// Complex rectangle with the padding summed in closed form (glynn_cesym.cu), for every
+// m <= 32: on complex Gaussian rectangles the padded walk cancels 10^6-fold already
+// at n - m = 1.
+int glynn_cesym_run(Call& c) {
+  const int block = glynn_cesym_block();
+  if (c.o.block > block) return PERM_EINVAL;
+  const int nb = c.o.block ? c.o.block : block;
+  const uint64_t g1 = 1ull << (c.m - 1);
+  const int bps = glynn_cesym_blocks_per_sm(c.m, c.n, nb);
+  if (bps <= 0) return PERM_ECUDA;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1, 1, kCplxRecord * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, g1, 0);
+  if (!c.o.chunk_log2) {
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 12;
+    while (k > 0 && (g1 >> k) < 128 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  static_assert(sizeof(CesymTable) <= kPartialsOffset - kFxTableOffset, "complex e_m table slot");
+  CesymTable* tab = reinterpret_cast<CesymTable*>(fx_table(c.h));
+  if (launch_glynn_cesym(a, tab, lc) != cudaSuccess) return PERM_ECUDA;
+  if (c.dErr && launch_write_double(-1.0, c.dErr, c.stream) != cudaSuccess) return PERM_ECUDA;
+  if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.m - 1, 0, 0.0,
+                         static_cast<double*>(c.dOut), nullptr, false, c.stream) != cudaSuccess)
+    return PERM_ECUDA;
+  return PERM_OK;
+}
+
 // Complex Glynn on the integer pipes (glynn_cfx.cu).
 int glynn_cfixed(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   if (c.o.block > 128) return PERM_EINVAL;
+  if (!raw && c.m < c.n && c.m <= glynn_cesym_max_m()) return glynn_cesym_run(c);
   const int block = c.n <= 40 ? 128 : 64;  // shared memory: 32 n^2 + 16 n per thread bytes
   // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
   const bool grouped = !raw && c.m < c.n;
@@ -486,6 +565,44 @@ int ryser_by_size(Call& c, unsigned long long total) {
   return PERM_OK;
 }
 
+// Real Ryser over the 2^n Gray-ordered subsets on the integer pipes (ryser_fx.cu):
+// exact fixed-point row sums, 64-bit-mantissa products, 192-bit accumulation.
+int ryser_fixed(Call& c) {
+  if (c.n > 62) return PERM_ETOOBIG;
+  const uint64_t terms = 1ull << c.n;
+  if (terms > (c.o.max_terms ? c.o.max_terms : (1ull << 44))) return PERM_ETOOBIG;
+  const bool want_abs = c.dErr != nullptr;
+  const int block = ryser_fx_block(c.m);
+  if (c.o.block > block) return PERM_EINVAL;
+  const int bps = ryser_fx_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, want_abs);
+  if (bps <= 0) return PERM_ECUDA;
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, (want_abs ? kCplxRecord : kRealRecord) * sizeof(double));
+  lc.stream = c.stream;
+  SweepArgs a = sweep_args(c, 0, terms, 12);
+  if (!c.o.chunk_log2) {
+    const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
+    int k = 12;
+    while (k > 2 && (terms >> k) < 1024 * warps) --k;
+    a.chunk_log2 = k;
+  }
+  // 2^40 maximal terms per 192-bit accumulator
+  if (a.chunk_log2 > 40) return PERM_ETOOBIG;
+  if (launch_ryser_fx(a, fx_table(c.h), lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // per term: m/2 pair products (< 2^-59 each), the binomial weight (< 2^-62), and the
+  // accumulation; the rounding of A to fixed point is bounded by the eta-widened sum
+  const double coef = std::ldexp((double)c.m + 6.0, -60);
+  const cudaError_t f = want_abs ? launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef,
+                                                       static_cast<double*>(c.dOut), c.dErr, false, c.stream)
+                                 : launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef,
+                                                      static_cast<double*>(c.dOut), nullptr, false, c.stream);
+  if (f != cudaSuccess) return PERM_ECUDA;
+  return PERM_OK;
+}
+
+bool real_ryser_on_integer_pipes(const Call& c) {
+  return c.o.arith == PERM_ARITH_FIXED || c.o.arith == PERM_ARITH_MIXED || (c.o.arith == PERM_ARITH_AUTO && c.n >= 10);
+}
+
 int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
   if (!raw && c.m < c.n) {
     // by size when the subsets of size <= m are few compared with all 2^n
@@ -493,6 +610,7 @@ int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
     for (int s = 1; s <= c.m; ++s) by_size += (long double)binomial_d(c.n, s);
     if (by_size * 3.0L < std::ldexp(1.0L, c.n) && by_size < 1.8e19L) return ryser_by_size(c, (unsigned long long)by_size);
   }
+  if (!raw && real_ryser_on_integer_pipes(c)) return ryser_fixed(c);
   if (c.n > 62) return PERM_ETOOBIG;
   const uint64_t terms = raw ? g1 - g0 : (1ull << c.n);
   if (!raw) g1 = terms;
@@ -501,7 +619,7 @@ int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
   const bool weighted = c.m < c.n;
   const int block = 256;
   int bps = ryser_f64_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, weighted, want_abs);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, kRealRecord * sizeof(double));
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, (want_abs ? kCplxRecord : kRealRecord) * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 14);
   SizeWeights w;
@@ -510,13 +628,23 @@ int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
     if (s <= c.n && s <= c.m) w.w[s] = (((c.m - s) & 1) ? -1.0 : 1.0) * binomial_d(c.n - s, c.m - s);
   }
   if (launch_ryser_f64(a, w, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // m - 1 product roundings, the weight, the Kahan sum against sum |term|; the row
+  // sums' own errors through the widened products (2 (m + 1) u for their evaluation)
   const double u = 1.1102230246251565e-16;
-  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
-  const double coef = u * ((double)c.m + 5.0 + 2.0 * (double)c.m * L);
+  const double coef = u * ((double)c.m + 5.0);
   const double sign = (!weighted && (c.n & 1)) ? -1.0 : 1.0;
-  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef, static_cast<double*>(c.dOut),
-                         c.dErr, raw, c.stream, sign) != cudaSuccess)
-    return PERM_ECUDA;
+  cudaError_t f;
+  if (want_abs) {
+    // the sign (-1)^n of the unweighted square sum is applied to the partial records
+    f = sign < 0 ? launch_negate_records(static_cast<double*>(a.partials), lc.grid, kCplxRecord, c.stream) : cudaSuccess;
+    if (f == cudaSuccess)
+      f = launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef, static_cast<double*>(c.dOut),
+                              c.dErr, raw, c.stream, 2.0 * u * (c.m + 1));
+  } else {
+    f = launch_finish_real(static_cast<const double*>(a.partials), lc.grid, 0, 0, coef, static_cast<double*>(c.dOut),
+                           nullptr, raw, c.stream, sign);
+  }
+  if (f != cudaSuccess) return PERM_ECUDA;
   return PERM_OK;
 }
 

@@ -11,6 +11,14 @@
 // grows with the depth of the tree, not with the number of leaves.  Prefix values are
 // combined in a Kahan sum (real, complex) or modulo 2^128 (integer; Gaussian integers
 // per part).
+//
+// The last three rows: below a node with three rows left, the subtree's value depends
+// only on the set of free columns.  For n <= 16 (not for Gaussian integers) the block
+// first tabulates, for every column triple a < b < c, the sum of the six products
+// a_{r0 x} a_{r1 y} a_{r2 z} over the orderings (x, y, z) of (a, b, c) -- the same
+// leaf products the search would form -- and the search stops three rows early,
+// adding the table entries of the triples of free columns.  That removes the three
+// deepest levels of the tree, which hold all but a sixth of its nodes.
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -96,17 +104,34 @@ __device__ __forceinline__ void kahan(double& acc, double& comp, double x) {
 }
 
 template <class F>
-__global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes) {
+__global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes, int tail) {
   typedef typename F::T T;
   extern __shared__ unsigned char smem_c[];
   __shared__ unsigned long long rowmask[kMaxN];
   const int n = a.n, m = a.m;
   T* sA = reinterpret_cast<T*>(smem_c);  // sA[i * n + j]
+  T* sT = sA + m * n;                    // tail: sT[(x * n + y) * n + z], x < y < z
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
     sA[idx] = F::load(a.A, i * a.rs + j * a.cs);
   }
   __syncthreads();
+  if (tail) {
+    const T* r0 = sA + (m - 3) * n;
+    const T* r1 = sA + (m - 2) * n;
+    const T* r2 = sA + (m - 1) * n;
+    for (int idx = threadIdx.x; idx < n * n * n; idx += blockDim.x) {
+      const int x = idx / (n * n), y = (idx / n) % n, z = idx % n;
+      if (!(x < y && y < z)) continue;
+      // the six orderings of (x, y, z) over rows r0, r1, r2
+      T v = F::mul(r0[x], F::add(F::mul(r1[y], r2[z]), F::mul(r1[z], r2[y])));
+      v = F::fma(r0[y], F::add(F::mul(r1[x], r2[z]), F::mul(r1[z], r2[x])), v);
+      v = F::fma(r0[z], F::add(F::mul(r1[x], r2[y]), F::mul(r1[y], r2[x])), v);
+      sT[idx] = v;
+    }
+    __syncthreads();
+  }
+  const unsigned long long allcols = (n == 64) ? ~0ull : ((1ull << n) - 1);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     unsigned long long mk = 0;
     for (int j = 0; j < n; ++j)
@@ -152,7 +177,29 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
       cand[k] = rowmask[k] & ~used;
       val[k] = F::zero();
       while (true) {
-        if (k == m - 1) {
+        if (tail && k == m - 3) {
+          // three rows left: the triples of free columns, from the table
+          T s = F::zero();
+          const unsigned long long fm = allcols & ~used;
+          unsigned long long xm = fm;
+          while (xm) {
+            const int x = __ffsll((long long)xm) - 1;
+            xm &= xm - 1;
+            unsigned long long ym = xm;
+            while (ym) {
+              const int y = __ffsll((long long)ym) - 1;
+              ym &= ym - 1;
+              unsigned long long zm = ym;
+              while (zm) {
+                const int z = __ffsll((long long)zm) - 1;
+                zm &= zm - 1;
+                s = F::add(s, sT[(x * n + y) * n + z]);
+              }
+            }
+          }
+          val[k] = s;
+          cand[k] = 0;
+        } else if (k == m - 1) {
           T s = F::zero();
           unsigned long long cm = cand[k];
           while (cm) {
@@ -258,13 +305,22 @@ void* pick(int dtype) {
 
 size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : dtype == 4 ? 32 : 16; }
 
+// the table of the last three rows: n <= 16, at least four rows, not Gaussian integers
+bool use_tail(int m, int n, int dtype) { return n <= 16 && m >= 4 && dtype != 4; }
+
+size_t smem_bytes(int m, int n, int dtype) {
+  const size_t cells = (size_t)m * n + (use_tail(m, n, dtype) ? (size_t)n * n * n : 0);
+  return cells * elem_bytes(dtype);
+}
+
 }  // namespace
 
 int combinatoric_blocks_per_sm(int m, int n, int dtype, int block) {
   void* k = pick(dtype);
   if (!k) return 0;
-  size_t smem = (size_t)m * n * elem_bytes(dtype);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem = smem_bytes(m, n, dtype);
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -273,7 +329,7 @@ int combinatoric_blocks_per_sm(int m, int n, int dtype, int block) {
 cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64_t prefixes, const LaunchCfg& c) {
   void* k = pick(dtype);
   if (!k) return cudaErrorInvalidValue;
-  size_t smem = (size_t)a.m * a.n * elem_bytes(dtype);
+  size_t smem = smem_bytes(a.m, a.n, dtype);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -281,7 +337,8 @@ cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64
   SweepArgs args = a;
   int d = depth;
   uint64_t p = prefixes;
-  void* params[] = {&args, &d, &p};
+  int t = use_tail(a.m, a.n, dtype) ? 1 : 0;
+  void* params[] = {&args, &d, &p, &t};
   return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
 }
 

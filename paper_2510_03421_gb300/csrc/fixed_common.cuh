@@ -41,7 +41,9 @@ __device__ __forceinline__ void mul_wide(u64 a, u64 b, u64& lo, u64& hi) {
 // E += 128 - lz.  h2 >= P / 2, so P is renormalised (clz) only every fourth pair and
 // after the last one.  Columns [N - K, N) are multiplied on the FP64 unit and the
 // double product is folded in once (its exponent field ed: value md 2^(ed - 1086)).
-template <int N, int K>
+// EXACT: magnitudes by two's complement (one more instruction per column), for the
+// variants that state an error bound; otherwise one's complement (below).
+template <int N, int K, bool EXACT = false>
 __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, int& E, unsigned& neg) {
   static_assert((N - K) % 2 == 0, "integer columns are taken in pairs");
   P = 1ull << 63;  // the value 1
@@ -54,7 +56,7 @@ __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, in
     neg ^= (unsigned)(sa ^ sb);
     // magnitudes by one's complement: |q| or |q| - 1, an error of one unit in a value
     // of up to 2^61 (relative 2^-58 or less for all but vanishing column sums)
-    const u64 aa = (u64)qa ^ sa, ab = (u64)qb ^ sb;
+    const u64 aa = EXACT ? ((u64)qa ^ sa) - sa : (u64)qa ^ sa, ab = EXACT ? ((u64)qb ^ sb) - sb : (u64)qb ^ sb;
     u64 lo, hi;
     mul_wide(aa, ab, lo, hi);
     // hi < 2^59, so lz >= 5; a pair product below 2^64 (vanishing column sums) keeps
@@ -91,6 +93,33 @@ __device__ __forceinline__ void soft_product(const long long (&S)[N], u64& P, in
   neg &= 1u;
 }
 
+// Product of (|S_j| + eta) over the first `nreal` sums (the others taken as they are),
+// computed in place with S restored afterwards: when every sum may be off by eta units
+// (the rounding of A to fixed point), |prod S_true - prod S| <= prod (|S| + eta) - prod |S|.
+template <int N, int K>
+__device__ __forceinline__ void soft_product_eta(long long (&S)[N], int nreal, long long eta, u64& P, int& E) {
+  u64 sg = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j < nreal) {
+      if (S[j] < 0) {
+        sg |= 1ull << j;
+        S[j] = -S[j];
+      }
+      S[j] += eta;
+    }
+  }
+  unsigned ng;
+  soft_product<N, K, true>(S, P, E, ng);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j < nreal) {
+      S[j] -= eta;
+      if ((sg >> j) & 1u) S[j] = -S[j];
+    }
+  }
+}
+
 // acc += (-1)^neg * P * 2^p (p = position of P's lsb in the accumulator, p <= 127)
 __device__ __forceinline__ void acc_add(u64& a0, u64& a1, u64& a2, u64 P, int p, unsigned neg) {
   u64 t0, t1, t2;
@@ -119,6 +148,29 @@ __device__ __forceinline__ void acc_add(u64& a0, u64& a1, u64& a2, u64 P, int p,
         : "+l"(a0), "+l"(a1), "+l"(a2)
         : "l"(t0), "l"(t1), "l"(t2));
   }
+}
+
+// acc += (-1)^neg * P * 2^p for 0 <= p <= 127 without branches: the lanes of a warp add
+// terms of different signs and positions at the same step, so a branch on either
+// diverges.  The three shifted words are chosen by masks; the sign enters as the
+// two's complement ~t + 1, with the + 1 as the carry into the lowest word (set by
+// adding the all-ones mask to itself).
+__device__ __forceinline__ void acc_add_nb(u64& a0, u64& a1, u64& a2, u64 P, int p, unsigned neg) {
+  const int s = p & 63;
+  const u64 lo = P << s;
+  const u64 hi = (P >> 1) >> (63 - s);  // P >> (64 - s), and 0 for s = 0
+  const u64 up = (u64)0 - (u64)(p >> 6);  // all ones when p >= 64
+  const u64 m = (u64)0 - (u64)(neg & 1u);
+  const u64 t0 = (lo & ~up) ^ m;
+  const u64 t1 = ((hi & ~up) | (lo & up)) ^ m;
+  const u64 t2 = (hi & up) ^ m;
+  asm("{\n\t.reg .u64 c;\n\t"
+      "add.cc.u64 c, %3, %3;\n\t"
+      "addc.cc.u64 %0, %0, %4;\n\t"
+      "addc.cc.u64 %1, %1, %5;\n\t"
+      "addc.u64 %2, %2, %6;\n\t}"
+      : "+l"(a0), "+l"(a1), "+l"(a2)
+      : "l"(m), "l"(t0), "l"(t1), "l"(t2));
 }
 
 // u64 binomial coefficient C(a, b), a <= 63 (exact: every partial product is a

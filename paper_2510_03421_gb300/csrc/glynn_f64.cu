@@ -27,7 +27,8 @@ namespace {
 template <int N, bool ABS>
 __global__ void __launch_bounds__(256) glynn_f64_kernel(SweepArgs a) {
   extern __shared__ double smem[];
-  __shared__ dd scratch[2 * 32];
+  __shared__ dd scratch[3 * 32];
+  __shared__ double s_eps[ABS ? N : 1];
   const int n = a.n, m = a.m;
   double* sP = smem;          // +2 a'_ij
   double* sM = smem + n * N;  // -2 a'_ij
@@ -39,6 +40,17 @@ __global__ void __launch_bounds__(256) glynn_f64_kernel(SweepArgs a) {
     sP[idx] = 2.0 * v;
     sM[idx] = -2.0 * v;
   }
+  if (ABS) {
+    // the rebuilt column sum errs by at most (n - 1) u sum_i |a'_ij| and each of the at
+    // most 2^chunk_log2 - 1 later updates by u |S_j| <= u sum_i |a'_ij| (first order)
+    const double steps = (double)n + ldexp(1.0, a.chunk_log2 < 62 ? a.chunk_log2 : 62);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double colabs = 0.0;
+      if (j < n)
+        for (int i = 0; i < n; ++i) colabs += fabs((i < m) ? A[i * a.rs + j * a.cs] : 1.0);
+      s_eps[j] = steps * 0x1p-53 * colabs * (1.0 + 0x1p-40);
+    }
+  }
   __syncthreads();
 
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -47,7 +59,7 @@ __global__ void __launch_bounds__(256) glynn_f64_kernel(SweepArgs a) {
   split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
   const uint64_t mask = (a.chunk_log2 >= 63) ? ~0ull : ((1ull << a.chunk_log2) - 1);
 
-  double acc = 0.0, comp = 0.0, absacc = 0.0;
+  double acc = 0.0, comp = 0.0, absacc = 0.0, diffacc = 0.0;
   double S[N];
   for (uint64_t s = 0; s < len; ++s, ++g) {
     if (s == 0 || (g & mask) == 0) {
@@ -74,17 +86,29 @@ __global__ void __launch_bounds__(256) glynn_f64_kernel(SweepArgs a) {
     const double sum = __dadd_rn(acc, y);
     comp = __dsub_rn(__dsub_rn(sum, acc), y);
     acc = sum;
-    if (ABS) absacc = __dadd_rn(absacc, fabs(t));
+    if (ABS) {
+      absacc = __dadd_rn(absacc, fabs(t));
+      // prod (|S_j| + eps_j) - |prod S_j| bounds the effect of the column sums' errors
+      double pe = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) pe = __dmul_rn(pe, __dadd_rn(fabs(S[j]), s_eps[j]));
+      diffacc = __dadd_rn(diffacc, __dsub_rn(pe, fabs(t)));
+    }
   }
 
-  dd v[2] = {two_sum(acc, -comp), dd{absacc, 0.0}};
-  block_sum_dd<2>(v, scratch);
+  // records {sum, sum |term|, sum of the widened differences} (the last two with ABS)
+  dd v[3] = {two_sum(acc, -comp), dd{absacc, 0.0}, dd{diffacc, 0.0}};
+  block_sum_dd<3>(v, scratch);
   if (threadIdx.x == 0) {
-    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * (ABS ? kCplxRecord : kRealRecord);
     rec[0] = v[0].hi;
     rec[1] = v[0].lo;
     rec[2] = v[1].hi;
     rec[3] = v[1].lo;
+    if (ABS) {
+      rec[4] = v[2].hi;
+      rec[5] = v[2].lo;
+    }
   }
 }
 
@@ -123,7 +147,10 @@ int glynn_f64_blocks_per_sm(int n, int block, bool want_abs) {
   void* k = pick(n, want_abs);
   if (!k) return 0;
   size_t smem = smem_bytes(n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;

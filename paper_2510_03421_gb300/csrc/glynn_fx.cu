@@ -17,7 +17,11 @@
 //     the otherwise idle FP64 unit (int64 -> double conversions and K - 1 DMUL,
 //     2^-53 each) and fold it into the mantissa once: the FP64 pipe and the integer
 //     pipes run side by side;
-//   * the signed terms are added into a 192-bit fixed-point accumulator per thread.
+//   * the signed terms are added into a 192-bit fixed-point accumulator per thread;
+//   * the error-bound variant (ABS) takes exact magnitudes of the column sums, adds up
+//     sum |term|, and, when some entry was rounded to fixed point, also
+//     prod_j (|S_j| + eta) (eta = m/2 units, the most a column sum can be off): the
+//     rounding of A moves a term by at most that product minus |term|.
 //     Its window is anchored on the thread's first nonzero term (whose leading bit
 //     lands on bit 120, leaving 120 bits below it and 70 above); a later term whose
 //     leading bit would pass bit 150 first shifts the window up.  Each thread's total
@@ -36,8 +40,11 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
   const double* A = static_cast<const double*>(a.A);
   __shared__ int xs[64];
   __shared__ int es[64];
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
+  __shared__ int bad, inexact;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    inexact = 0;
+  }
   __syncthreads();
   const int j = threadIdx.x;
   if (j < n) {
@@ -57,8 +64,13 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
     es[j] = e;
     for (int i = 0; i < n; ++i) {
       long long q = 0;
-      if (i < m) q = llrint(ldexp(A[i * a.rs + j * a.cs], e));
-      else q = (long long)llrint(ldexp(1.0, e));
+      if (i < m) {
+        const double sv = ldexp(A[i * a.rs + j * a.cs], e);
+        if (isfinite(sv) && rint(sv) != sv) inexact = 1;
+        q = llrint(sv);
+      } else {
+        q = (long long)llrint(ldexp(1.0, e));
+      }
       tab->d[i * 64 + j] = 2 * q;
     }
   }
@@ -72,16 +84,21 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
     tab->e_max = xsum;
     tab->e_sum = esum;
     tab->bad = bad;
+    tab->inexact = inexact;
   }
 }
 
 template <int N, int K, bool ABS>
 __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   extern __shared__ long long smem_fx[];
-  __shared__ dd scratch[2 * 32];
+  __shared__ dd scratch[3 * 32];
   const int n = a.n;
   long long* sP = smem_fx;          // +2 q_ij
   long long* sM = smem_fx + n * N;  // -2 q_ij
+  // error-bound variant with inexact quantisation: each column sum may be off by eta
+  // units (m real rows rounded by half a unit each)
+  const bool use_eta = ABS && tab->inexact != 0;
+  const long long eta = (a.m + 1) / 2;
   for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
     const int i = idx / N, j = idx - i * N;
     const long long v = (j < n) ? tab->d[i * 64 + j] : 0;
@@ -109,6 +126,29 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(Swee
   bool anchored = false;
   u64 a0 = 0, a1 = 0, a2 = 0;
   u64 b0 = 0, b1 = 0, b2 = 0;  // sum of |term| (ABS only)
+  u64 c0 = 0, c1 = 0, c2 = 0;  // sum of prod (|S| + eta) (ABS with inexact quantisation)
+  // add P 2^(E - 63 - e_sum) (sign neg) into (x0, x1, x2), moving the window up if needed
+  auto add_term = [&](u64& x0, u64& x1, u64& x2, u64 P, int E, unsigned neg) {
+    if (!anchored) {
+      e_lo = E - e_sum - kAnchorBit;
+      anchored = true;
+    }
+    int p = E - 63 - e_sum - e_lo;
+    if (p > kMaxLsb) {  // rare: move the window up
+      shr192(a0, a1, a2, p - kMaxLsb);
+      if (ABS) {
+        shr192(b0, b1, b2, p - kMaxLsb);
+        shr192(c0, c1, c2, p - kMaxLsb);
+      }
+      e_lo += p - kMaxLsb;
+      p = kMaxLsb;
+    }
+    if (p >= 0) {
+      acc_add_nb(x0, x1, x2, P, p, neg);
+    } else {  // a term far below the window (rare): its low bits fall off
+      acc_add(x0, x1, x2, P, p, neg);
+    }
+  };
   long long S[N];
   for (uint64_t r = warp; r < rounds; r += warps) {
     const uint64_t chunk = c_first + 32 * r + lane;
@@ -139,34 +179,35 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(Swee
       u64 P;
       int E;
       unsigned neg;
-      soft_product<N, K>(S, P, E, neg);
+      soft_product<N, K, ABS>(S, P, E, neg);  // exact magnitudes in the bound variant
       if (P != 0) {
-        if (!anchored) {
-          e_lo = E - e_sum - kAnchorBit;
-          anchored = true;
-        }
-        int p = E - 63 - e_sum - e_lo;
-        if (p > kMaxLsb) {  // rare: move the window up
-          shr192(a0, a1, a2, p - kMaxLsb);
-          if (ABS) shr192(b0, b1, b2, p - kMaxLsb);
-          e_lo += p - kMaxLsb;
-          p = kMaxLsb;
-        }
-        acc_add(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u));
-        if (ABS) acc_add(b0, b1, b2, P, p, 0u);
+        add_term(a0, a1, a2, P, E, neg ^ (unsigned)(g & 1u));
+        if (ABS) add_term(b0, b1, b2, P, E, 0u);
+      }
+      if (use_eta) {
+        u64 Pe;
+        int Ee;
+        soft_product_eta<N, K>(S, n, eta, Pe, Ee);
+        if (Pe != 0) add_term(c0, c1, c2, Pe, Ee, 0u);
       }
     }
   }
 
-  dd v[2] = {to_dd(a0, a1, a2, e_lo), ABS ? to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0}};
-  block_sum_dd<2>(v, scratch);
+  // records {sum, sum |term|, sum prod (|S| + eta)} (the last two with ABS only)
+  dd v[3] = {to_dd(a0, a1, a2, e_lo), ABS ? to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0},
+             use_eta ? to_dd(c0, c1, c2, e_lo) : dd{0.0, 0.0}};
+  block_sum_dd<3>(v, scratch);
   if (threadIdx.x == 0) {
-    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
     const bool bad = tab->bad != 0;  // a non-finite entry: no fixed-point image exists
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * (ABS ? kCplxRecord : kRealRecord);
     rec[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v[0].hi;
     rec[1] = bad ? 0.0 : v[0].lo;
     rec[2] = v[1].hi;
     rec[3] = v[1].lo;
+    if (ABS) {
+      rec[4] = v[2].hi;
+      rec[5] = v[2].lo;
+    }
   }
 }
 

@@ -21,8 +21,12 @@ namespace {
 template <int N>
 __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fxg_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   const bool ABS = a.want_abs != 0;
+  // with an error bound and inexact quantisation: a column sum's rounding is at most
+  // m/2 units (the padding rows are exact)
+  const bool use_eta = ABS && tab->inexact != 0;
+  const long long eta = (a.m + 1) / 2;
   extern __shared__ long long smem_fx[];
-  __shared__ dd scratch[2 * 32];
+  __shared__ dd scratch[3 * 32];
   __shared__ u64 s_wm[64];  // C(n - m, t) = s_wm[t] 2^(s_we[t] - 64), s_wm normalised
   __shared__ int s_we[64];
   const int n = a.n, m = a.m, k = n - m;
@@ -58,6 +62,30 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fxg_kernel(Sweep
   bool anchored = false;
   u64 a0 = 0, a1 = 0, a2 = 0;
   u64 b0 = 0, b1 = 0, b2 = 0;
+  u64 c0 = 0, c1 = 0, c2 = 0;
+  auto add_term = [&](u64& x0, u64& x1, u64& x2, u64 P, int E, unsigned neg) {
+    if (!anchored) {
+      e_lo = E - e_sum - kAnchorBit;
+      anchored = true;
+    }
+    int p = E - 63 - e_sum - e_lo;
+    if (p > kMaxLsb) {
+      shr192(a0, a1, a2, p - kMaxLsb);
+      if (ABS) {
+        shr192(b0, b1, b2, p - kMaxLsb);
+        shr192(c0, c1, c2, p - kMaxLsb);
+      }
+      e_lo += p - kMaxLsb;
+      p = kMaxLsb;
+    }
+    acc_add(x0, x1, x2, P, p, neg);
+  };
+  auto weigh = [&](u64& P, int& E, int t) {
+    const u64 h2 = __umul64hi(P, s_wm[t]);
+    const int top = (int)(h2 >> 63);
+    P = top ? h2 : (h2 << 1);
+    E += s_we[t] - 1 + top;
+  };
   long long S[N];
   for (uint64_t r = warp; r < rounds; r += warps) {
     const uint64_t chunk = c_first + 32 * r + lane;
@@ -98,39 +126,44 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fxg_kernel(Sweep
         u64 P;
         int E;
         unsigned neg;
-        soft_product<N, 0>(S, P, E, neg);
+        if (ABS) {
+          soft_product<N, 0, true>(S, P, E, neg);  // exact magnitudes in the bound variant
+        } else {
+          soft_product<N, 0>(S, P, E, neg);
+        }
         if (P != 0) {
-          const u64 h2 = __umul64hi(P, s_wm[t]);
-          const int top = (int)(h2 >> 63);
-          P = top ? h2 : (h2 << 1);
-          E += s_we[t] - 1 + top;
-          if (!anchored) {
-            e_lo = E - e_sum - kAnchorBit;
-            anchored = true;
+          weigh(P, E, t);
+          add_term(a0, a1, a2, P, E, neg ^ (unsigned)(g & 1u) ^ (unsigned)(t & 1));
+          if (ABS) add_term(b0, b1, b2, P, E, 0u);
+        }
+        if (use_eta) {
+          u64 Pe;
+          int Ee;
+          soft_product_eta<N, 0>(S, n, eta, Pe, Ee);
+          if (Pe != 0) {
+            weigh(Pe, Ee, t);
+            add_term(c0, c1, c2, Pe, Ee, 0u);
           }
-          int p = E - 63 - e_sum - e_lo;
-          if (p > kMaxLsb) {
-            shr192(a0, a1, a2, p - kMaxLsb);
-            if (ABS) shr192(b0, b1, b2, p - kMaxLsb);
-            e_lo += p - kMaxLsb;
-            p = kMaxLsb;
-          }
-          acc_add(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u) ^ (unsigned)(t & 1));
-          if (ABS) acc_add(b0, b1, b2, P, p, 0u);
         }
       }
     }
   }
 
-  dd v[2] = {to_dd(a0, a1, a2, e_lo), ABS ? to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0}};
-  block_sum_dd<2>(v, scratch);
+  dd v[3] = {to_dd(a0, a1, a2, e_lo), ABS ? to_dd(b0, b1, b2, e_lo) : dd{0.0, 0.0},
+             use_eta ? to_dd(c0, c1, c2, e_lo) : dd{0.0, 0.0}};
+  block_sum_dd<3>(v, scratch);
   if (threadIdx.x == 0) {
-    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+    // records {sum, sum |term|, eta-widened sum}: kCplxRecord doubles with a bound
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * (ABS ? kCplxRecord : kRealRecord);
     const bool bad = tab->bad != 0;
     rec[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v[0].hi;
     rec[1] = bad ? 0.0 : v[0].lo;
     rec[2] = v[1].hi;
     rec[3] = v[1].lo;
+    if (ABS) {
+      rec[4] = v[2].hi;
+      rec[5] = v[2].lo;
+    }
   }
 }
 

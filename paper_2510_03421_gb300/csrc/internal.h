@@ -48,10 +48,10 @@ int glynn_dmma_max_n();
 // preparation kernel derives on the device.
 struct FxTable {
   long long d[64 * 64];
-  int e_max;  // sum_j x_j with sum_i |a'_ij| < 2^x_j
-  int e_sum;  // sum_j e_j (column j scaled by 2^e_j)
-  int bad;    // a non-finite entry was seen
-  int pad;
+  int e_max;    // sum_j x_j with sum_i |a'_ij| < 2^x_j
+  int e_sum;    // sum_j e_j (column j scaled by 2^e_j)
+  int bad;      // a non-finite entry was seen
+  int inexact;  // some entry was rounded when scaled to fixed point
 };
 // mixed: the last glynn_fx_mixed_columns(n) columns' product runs on the FP64 unit
 cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream);
@@ -63,6 +63,38 @@ int glynn_fx_block(int n);  // threads per block of the square kernel (its launc
 // n - m + 1 terms each
 cudaError_t launch_glynn_fxg(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
 int glynn_fxg_blocks_per_sm(int m, int n, int block);
+
+// rectangular walk with the padding summed in closed form (1 <= m <= glynn_esym_max_m(),
+// m < n; glynn_esym.cu): g ranges over [0, 2^(m-1)); records of kCplxRecord doubles
+// {sum, sum e_m(|c|), quantisation term} (unnormalised), reduced by launch_esym_finish
+struct EsymTable {
+  long long d[64 * 64];  // +2 q_ij at d[i * 64 + j] (rows i < m)
+  int e[64];             // column j is held as q_ij = a_ij 2^e[j]
+  int bad;               // a non-finite entry was seen
+  int inexact;           // some a_ij 2^e[j] was not an integer (rounded)
+  int eta;               // bound on a column sum's quantisation error, in units
+  int pad;
+};
+cudaError_t launch_glynn_esym(const SweepArgs& a, EsymTable* tab, const LaunchCfg& c, bool want_abs);
+int glynn_esym_blocks_per_sm(int m, int n, int block, bool want_abs);
+int glynn_esym_max_m();
+int glynn_esym_block();
+// out = sum / 2^(m-1); err = coef * G + F + the rounding of out (err may be null)
+cudaError_t launch_esym_finish(const double* rec, int nrec, int m, double coef, double* out, double* err,
+                               cudaStream_t s);
+
+// complex rectangles with the padding summed in closed form (glynn_cesym.cu): same
+// index range and records as the complex sweeps (kCplxRecord, no error term)
+struct CesymTable {
+  long long d[2 * 64 * 64];  // (re, im) of +2 q_ij at d[2 (i * 64 + j)]
+  int e[64];
+  int bad;
+  int pad;
+};
+cudaError_t launch_glynn_cesym(const SweepArgs& a, CesymTable* tab, const LaunchCfg& c);
+int glynn_cesym_blocks_per_sm(int m, int n, int block);
+int glynn_cesym_max_m();
+int glynn_cesym_block();
 
 // --- Glynn, complex input on the integer pipes (glynn_cfx.cu); n <= glynn_cfx_max_n()
 struct CfxTable {
@@ -100,6 +132,11 @@ struct SizeWeights {
   double w[65];
 };
 cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, const LaunchCfg& c, bool want_abs);
+// Ryser on the integer pipes (ryser_fx.cu), real input, 1 <= m <= n <= 62: g over the
+// 2^n Gray-ordered subsets, weights (-1)^(m-s) C(n-s, m-s); kRealRecord records
+cudaError_t launch_ryser_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);
+int ryser_fx_blocks_per_sm(int m, int n, int block, bool want_abs);
+int ryser_fx_block(int m);
 // c[s] = number of nonempty subsets of size < s (c[1] = 0): start of size s in the
 // global index of the by-size Ryser enumeration
 struct SizeCounts {
@@ -215,6 +252,12 @@ cudaError_t launch_batched_int(const void* packed, const int64_t* offsets, const
 cudaError_t launch_finish_real(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
                                double* err, bool raw, cudaStream_t s, double sign = 1.0);
 
+// records {sum, sum |term|, sum of the eta-widened products} (kCplxRecord doubles, the
+// integer-pipe sweeps with an error bound): see reduce.cu
+cudaError_t launch_finish_bound(const double* rec, int nrec, int pow2, int fact_of, double coef, double* out,
+                                double* err, bool raw, cudaStream_t s, double diff_coef = 0.0);
+// negate the leading double-double of each record (stride doubles apart)
+cudaError_t launch_negate_records(double* rec, int nrec, int stride, cudaStream_t s);
 cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
                                double* err, bool raw, cudaStream_t s);
 cudaError_t launch_finish_int(const unsigned long long* rec, int nrec, int pow2, int fact_of, unsigned long long* out,

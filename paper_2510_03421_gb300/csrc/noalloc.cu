@@ -9,7 +9,9 @@
 //
 // Host code cannot use the array's name as a device address (in host code it names
 // a host-side stand-in), so the address is looked up with cudaGetSymbolAddress once
-// per device, with that device current, on the first call on that device.
+// per device, with that device current, on the first call on that device, and kept
+// for the life of the process: a cudaDeviceReset discards the array with the
+// context, so after one this entry point must not be called again in that process.
 #include <cstdint>
 #include <mutex>
 
@@ -46,13 +48,15 @@ int scratch_for_current_device(double** out) {
   return PERM_OK;
 }
 
-bool device_accessible(const void* p) {
+// Device or managed memory of device `dev` (a kernel on `dev` may read it); host memory
+// and another GPU's memory are refused before anything is launched.
+bool on_this_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -66,7 +70,9 @@ extern "C" int perm_glynn_noalloc(const void* A, int64_t m, int64_t n, int64_t l
   if (m > 64 || n > 64) return PERM_ETOOBIG;
   if (grid < 0) return PERM_EINVAL;
   if (grid > kNoAllocMaxBlocks) return PERM_ETOOBIG;
-  if (!device_accessible(out) || (m > 0 && n > 0 && !device_accessible(A))) return PERM_EINVAL;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return PERM_ECUDA;
+  if (!on_this_device(out, cur) || (m > 0 && n > 0 && !on_this_device(A, cur))) return PERM_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
@@ -102,8 +108,9 @@ extern "C" int perm_glynn_noalloc(const void* A, int64_t m, int64_t n, int64_t l
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return PERM_ECUDA;
-    int bps = glynn_f64_blocks_per_sm(a.n, lc.block, false);
-    grid = sms * (bps > 0 ? bps : 1);
+    const int bps = glynn_f64_blocks_per_sm(a.n, lc.block, false);
+    if (bps <= 0) return PERM_ECUDA;  // the kernel's shared-memory limit could not be raised
+    grid = sms * bps;
     const uint64_t want = (terms + 256u * 16u - 1) / (256u * 16u);
     if (want < (uint64_t)grid) grid = (int)want;
     if (grid > kNoAllocMaxBlocks) grid = kNoAllocMaxBlocks;

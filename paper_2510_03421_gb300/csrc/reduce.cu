@@ -69,6 +69,50 @@ __global__ void finish_cplx_kernel(const double* rec, int nrec, int pow2, int fa
   if (err) err[0] = err_coef * v[2].hi + fabs(__dsub_rn(re, v[0].hi) - v[0].lo) + fabs(__dsub_rn(im, v[1].hi) - v[1].lo);
 }
 
+// Records {sum, G, Ge} of kCplxRecord doubles (sum |term| G, and Ge = sum of the
+// products of (|S| + eta) when the rounding of A to fixed point was inexact, else 0):
+// out = sum / (2^pow2 fact_of!) (raw: the unnormalised double-double); err = coef G,
+// plus, when Ge != 0, (Ge - G) + coef (G + Ge) for the rounding of A and of the two
+// bound sums themselves, plus the rounding of out.
+//   diff_coef > 0: the third slot is instead the sum D of the per-term differences
+//   (widened product - |term|) formed in FP64, and err = coef G + D (1 + 2^-25) +
+//   diff_coef (G + D) (the two FP64 products behind each difference).
+__global__ void finish_bound_kernel(const double* rec, int nrec, int pow2, int fact_of, double coef, double* out,
+                                    double* err, int raw, double diff_coef) {
+  __shared__ dd scratch[3 * 32];
+  dd v[3] = {dd{0.0, 0.0}, dd{0.0, 0.0}, dd{0.0, 0.0}};
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = dd_add(v[k], dd{rec[kCplxRecord * r + 2 * k], rec[kCplxRecord * r + 2 * k + 1]});
+  }
+  block_sum_dd<3>(v, scratch);
+  if (threadIdx.x != 0) return;
+  if (!raw) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = dd_ldexp(v[k], -pow2);
+    for (int f = 2; f <= fact_of; ++f)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = dd_div_d(v[k], (double)f);
+  }
+  const double G = v[1].hi, Ge = v[2].hi;
+  double e = coef * G;
+  if (diff_coef > 0.0) {
+    const double D = fmax(Ge, 0.0);
+    e += D * (1.0 + 0x1p-25) + diff_coef * (G + D);
+  } else if (Ge != 0.0) {
+    e += fmax(__dsub_rn(Ge, G), 0.0) * (1.0 + 0x1p-50) + coef * (G + Ge);
+  }
+  if (raw) {
+    out[0] = v[0].hi;
+    out[1] = v[0].lo;
+    if (err) err[0] = e;
+    return;
+  }
+  const double r = __dadd_rn(v[0].hi, v[0].lo);
+  out[0] = r;
+  if (err) err[0] = e + fabs(__dsub_rn(r, v[0].hi) - v[0].lo);
+}
+
 __global__ void finish_int_kernel(const unsigned long long* rec, int nrec, int pow2, int fact_of,
                                   unsigned long long* out, int raw) {
   __shared__ u128 part[256];
@@ -153,6 +197,24 @@ cudaError_t launch_finish_real(const double* rec, int nrec, int pow2, int fact_o
 cudaError_t launch_finish_cplx(const double* rec, int nrec, int pow2, int fact_of, double err_coef, double* out,
                                double* err, bool raw, cudaStream_t s) {
   finish_cplx_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, err_coef, out, err, raw ? 1 : 0);
+  return cudaGetLastError();
+}
+
+__global__ void negate_records_kernel(double* rec, int nrec, int stride) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
+    rec[(size_t)r * stride] = -rec[(size_t)r * stride];
+    rec[(size_t)r * stride + 1] = -rec[(size_t)r * stride + 1];
+  }
+}
+
+cudaError_t launch_negate_records(double* rec, int nrec, int stride, cudaStream_t s) {
+  negate_records_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(rec, nrec, stride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_bound(const double* rec, int nrec, int pow2, int fact_of, double coef, double* out,
+                                double* err, bool raw, cudaStream_t s, double diff_coef) {
+  finish_bound_kernel<<<1, 256, 0, s>>>(rec, nrec, pow2, fact_of, coef, out, err, raw ? 1 : 0, diff_coef);
   return cudaGetLastError();
 }
 

@@ -20,8 +20,9 @@ namespace {
 template <int M, bool WEIGHTED, bool ABS>
 __global__ void __launch_bounds__(256) ryser_f64_kernel(SweepArgs a, SizeWeights weights) {
   extern __shared__ double smem[];
-  __shared__ dd scratch[2 * 32];
+  __shared__ dd scratch[3 * 32];
   __shared__ double w[65];
+  __shared__ double s_eps[ABS ? M : 1];
   const int n = a.n, m = a.m;
   double* sP = smem;          // sP[c * M + i] = +a_ic
   double* sM = smem + n * M;  // -a_ic
@@ -34,6 +35,17 @@ __global__ void __launch_bounds__(256) ryser_f64_kernel(SweepArgs a, SizeWeights
   }
   if (WEIGHTED)
     for (int s = threadIdx.x; s <= n; s += blockDim.x) w[s] = weights.w[s];
+  if (ABS) {
+    // a rebuilt row sum errs by at most (n - 1) u sum_j |a_ij|, each of the at most
+    // 2^chunk_log2 - 1 later updates by u sum_j |a_ij| (first order)
+    const double steps = (double)n + ldexp(1.0, a.chunk_log2 < 62 ? a.chunk_log2 : 62);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      double rowabs = 0.0;
+      if (i < m)
+        for (int c = 0; c < n; ++c) rowabs += fabs(A[i * a.rs + c * a.cs]);
+      s_eps[i] = steps * 0x1p-53 * rowabs * (1.0 + 0x1p-40);
+    }
+  }
   __syncthreads();
 
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -42,7 +54,7 @@ __global__ void __launch_bounds__(256) ryser_f64_kernel(SweepArgs a, SizeWeights
   split_range(a.g_begin, a.g_end, nt, tid, &g, &len);
   const uint64_t mask = (a.chunk_log2 >= 63) ? ~0ull : ((1ull << a.chunk_log2) - 1);
 
-  double acc = 0.0, comp = 0.0, absacc = 0.0;
+  double acc = 0.0, comp = 0.0, absacc = 0.0, diffacc = 0.0;
   double R[M];
   int size = 0;
   for (uint64_t s = 0; s < len; ++s, ++g) {
@@ -77,17 +89,33 @@ __global__ void __launch_bounds__(256) ryser_f64_kernel(SweepArgs a, SizeWeights
     const double sum = __dadd_rn(acc, y);
     comp = __dsub_rn(__dsub_rn(sum, acc), y);
     acc = sum;
-    if (ABS) absacc = __dadd_rn(absacc, fabs(t));
+    if (ABS) {
+      absacc = __dadd_rn(absacc, fabs(t));
+      // |weight| (prod (|R_i| + eps_i) - prod |R_i|): the row sums' own errors
+      double pe = 1.0, pa = 1.0;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        pe = __dmul_rn(pe, __dadd_rn(fabs(R[i]), s_eps[i]));
+        pa = __dmul_rn(pa, fabs(R[i]));
+      }
+      const double aw = WEIGHTED ? fabs(w[size]) : 1.0;
+      diffacc = __dadd_rn(diffacc, __dmul_rn(aw, __dsub_rn(pe, pa)));
+    }
   }
 
-  dd v[2] = {two_sum(acc, -comp), dd{absacc, 0.0}};
-  block_sum_dd<2>(v, scratch);
+  // records {sum, sum |term|, sum of the widened differences} (the last two with ABS)
+  dd v[3] = {two_sum(acc, -comp), dd{absacc, 0.0}, dd{diffacc, 0.0}};
+  block_sum_dd<3>(v, scratch);
   if (threadIdx.x == 0) {
-    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * (ABS ? kCplxRecord : kRealRecord);
     rec[0] = v[0].hi;
     rec[1] = v[0].lo;
     rec[2] = v[1].hi;
     rec[3] = v[1].lo;
+    if (ABS) {
+      rec[4] = v[2].hi;
+      rec[5] = v[2].lo;
+    }
   }
 }
 
