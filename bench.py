@@ -179,6 +179,21 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- batched leg
+# Per padded order N of the mixed integer-pipe sweep glynn_fx_kernel<N, K, false>: thread
+# instructions per term (ncu smsp__inst_executed.sum x 32 / terms), DRAM bytes per launch
+# and pipe utilisations, from one ncu capture of this kernel (label says which); the
+# bench times the kernel itself and scales by its own terms/s.
+ISSUE_PROFILE = {
+    36: {"instructions_per_term": 896.0, "dram_bytes_per_launch": 562688,
+         "pipes": {"alu": 0.628, "fp64": 0.614, "fma": 0.276, "issue": 0.573},
+         "label": "ncu capture of glynn_fx_kernel<36, 8, false> at n = 34 (instructions scale per term; "
+                  "DRAM traffic does not grow with the term count)"},
+}
+
+
+BATCH_CHECK = {}  # results of the batched leg kept for the oracle check of the CPU leg
+
+
 def run_batched(args, dev, stream):
     """100,000 complex128 n x n blocks of Haar unitaries (n uniform in 4..20): one
     perm_batched graph launch per step, against one perm_glynn call per matrix."""
@@ -206,21 +221,43 @@ def run_batched(args, dev, stream):
             ev[k][1].record(stream)
         stream.synchronize()
     batched_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    # plain: one perm_glynn launch per matrix on the same stream
+    # plain: one perm_glynn call per matrix (its own kernel launches, default arithmetic),
+    # on a sample of the batch, captured once into a CUDA graph and replayed, so that the
+    # time is the kernels' and not the host's; the same again with opts.arith = FP64
+    sample = min(count, 10000)
     views = [tp[int(offsets[b]): int(offsets[b]) + int(sizes[b]) ** 2].view(int(sizes[b]), int(sizes[b]))
-             for b in range(count)]
-    plain = torch.empty((count, 2), dtype=torch.float64, device=dev)
-    outs = [plain[b] for b in range(count)]
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for b in range(count):
-        capi.perm_glynn(views[b], out=outs[b], stream=stream)
-    stream.synchronize()
-    plain_s = time.perf_counter() - t0
+             for b in range(sample)]
+    plain = {}
+    for key, opts in (("default", None), ("fp64", dict(arith=capi.PERM_ARITH_FP64))):
+        res = torch.empty((sample, 2), dtype=torch.float64, device=dev)
+        outs = [res[b] for b in range(sample)]
+        for b in range(sample):  # eager pass: per-call set-up, and the workspace sized
+            capi.perm_glynn(views[b], out=outs[b], stream=stream, opts=opts)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+            for b in range(sample):
+                capi.perm_glynn(views[b], out=outs[b], stream=stream, opts=opts)
+        graph.replay()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(max(1, args.steps // 4)):
+                graph.replay()
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.steps // 4)
+        plain[key] = {"perms_per_s": sample / (ms * 1e-3), "ms_per_sample": ms, "values": res.cpu().numpy()}
+        del graph
     a = out.cpu().numpy()
-    p = plain.cpu().numpy()
-    za, zp = a[:, 0] + 1j * a[:, 1], p[:, 0] + 1j * p[:, 1]
+    p = plain["default"]["values"]
+    za, zp = a[:sample, 0] + 1j * a[:sample, 1], p[:, 0] + 1j * p[:, 1]
     rel = float(np.max(np.abs(za - zp) / np.maximum(np.abs(zp), 1e-300)))
+    BATCH_CHECK["batched"] = a
+    BATCH_CHECK["plain"] = p
+    BATCH_CHECK["sizes"], BATCH_CHECK["packed"], BATCH_CHECK["offsets"] = sizes, packed, offsets
+    batched_rate = count / (batched_ms * 1e-3)
     terms = float(np.sum(2.0 ** (sizes.astype(np.float64) - 1)))
     # algorithmic work of the complex Glynn sweep: 8n - 4 FP64-equivalent operations per term
     flops = float(np.sum(2.0 ** (sizes.astype(np.float64) - 1) * (8.0 * sizes - 4.0)))
@@ -228,8 +265,12 @@ def run_batched(args, dev, stream):
             "perms_per_s": count / (batched_ms * 1e-3), "ms_per_batch": batched_ms,
             "terms_per_s": terms / (batched_ms * 1e-3),
             "fp64_equiv_tflops": flops / (batched_ms * 1e-3) / 1e12,
-            "plain_perms_per_s": count / plain_s, "plain_s": plain_s,
-            "speedup_vs_plain": plain_s / (batched_ms * 1e-3),
+            "plain_kernel": {"perms_per_s": plain["default"]["perms_per_s"],
+                             "fp64_perms_per_s": plain["fp64"]["perms_per_s"], "sample": sample,
+                             "how": "one perm_glynn per matrix (default arithmetic; and opts.arith = FP64) for the "
+                                    "first %d matrices, captured in one CUDA graph, replayed, CUDA events" % sample},
+            "speedup_vs_plain_kernel": batched_rate / plain["default"]["perms_per_s"],
+            "speedup_vs_plain_fp64_kernel": batched_rate / plain["fp64"]["perms_per_s"],
             "max_rel_diff_vs_plain": rel,
             "arith": "n >= 13: integer pipes (fixed-point column sums, complex software-float products, 192-bit "
                      "accumulation; the tuner may put part of each product on the FP64 unit); below: FP64, "
@@ -392,7 +433,9 @@ def run_precision(dev, stream, cases=((8, 8), (16, 16), (24, 24), (32, 32), (8, 
         if m == n:
             x, y = inputs.cauchy_points(n, inputs.SEED_BASE + 20 + n, draws=100)
             dx, dy = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
-            t = float(capi.perm_cauchy(dx, dy, stream=stream)[0].item())
+            tout = capi.perm_cauchy(dx, dy, stream=stream)
+            stream.synchronize()  # the result is written on `stream`; read it after that
+            t = float(tout[0].item())
             fams.append(("cauchy", 1.0 / (x[0][:, None] - y[0][None, :]), t))
         for name, A, truth in fams:
             row = {"matrix": "%s %dx%d" % (name, m, n), "true": truth}
@@ -408,34 +451,88 @@ def run_precision(dev, stream, cases=((8, 8), (16, 16), (24, 24), (32, 32), (8, 
     return {"metric": "digits lost, Eq. digits_lost (None = exact)", "cases": rows}
 
 
+def _oracle_glynn(A):
+    import oracle
+    return complex(oracle.glynn(A))
+
+
+def batched_oracle_check():
+    """CPU leg: both arms of the batched comparison against the long-double oracle, two
+    matrices of every order 4..20 from the plain arm's sample (spawned processes)."""
+    import multiprocessing
+
+    import numpy as np
+    sizes, packed, offsets = BATCH_CHECK["sizes"], BATCH_CHECK["packed"], BATCH_CHECK["offsets"]
+    sample = len(BATCH_CHECK["plain"])
+    picks = []
+    for n in range(4, 21):
+        idx = np.nonzero(sizes[:sample] == n)[0]
+        if len(idx):
+            picks += sorted({int(idx[0]), int(idx[-1])})
+    mats = [np.ascontiguousarray(packed[offsets[b]: offsets[b] + int(sizes[b]) ** 2].reshape(int(sizes[b]),
+                                                                                         int(sizes[b])))
+            for b in picks]
+    t0 = time.time()
+    with multiprocessing.get_context("spawn").Pool(min(len(mats), os.cpu_count() or 1)) as pool:
+        truth = pool.map(_oracle_glynn, mats)
+    res = {}
+    for arm in ("batched", "plain"):
+        v = BATCH_CHECK[arm]
+        errs = [abs(complex(v[b, 0], v[b, 1]) - t) / abs(t) for b, t in zip(picks, truth)]
+        res["max_rel_err_vs_oracle_" + arm] = float(max(errs))
+    res["checked"] = "%d matrices, two of every order 4..20, oracle in long double (%.0f s)" % (len(picks),
+                                                                                          time.time() - t0)
+    return res
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
-    """Time one perm_glynn (default arithmetic) per step on each of the other workloads:
-    16x16 float64, 32x32 complex128, 20x40 float64 (grouped rectangular walk) and
-    26x26 0/1 (exact int128).  CUDA events, best of `reps` after a warm-up."""
+    """Time each of the other workloads (CUDA events, best of `reps` after a warm-up):
+    16x16 float64 by Glynn, Ryser and the combinatoric algorithm (16! injective maps);
+    32x32 complex128 by Glynn; 20x40 float64 by Glynn (padding summed in closed form)
+    and by rectangular Ryser (2^40 Gray-ordered subsets on the integer pipes); 26x26 0/1
+    (exact int128) by Glynn."""
     import torch
 
     from paper_2510_03421_gb300 import capi, inputs
-    cases = [("16x16 float64 uniform[-1,1]", inputs.square16_f64(), 1 << 15),
-             ("32x32 complex128 Gaussian / sqrt(2n)", inputs.square32_c128(), 1 << 31),
-             ("20x40 float64 uniform[0,1] (grouped: 2^19 x 21 terms)", inputs.rect20x40_f64(), (1 << 19) * 21),
-             ("26x26 0/1 Bernoulli(0.5), exact", inputs.square26_01(), 1 << 25)]
+    A16, R = inputs.square16_f64(), inputs.rect20x40_f64()
+    cases = [("16x16 float64 uniform[-1,1], Glynn", "perm_glynn", A16, None, 1 << 15, reps),
+             ("16x16 float64 uniform[-1,1], Ryser", "perm_ryser", A16, None, 1 << 16, reps),
+             ("16x16 float64 uniform[-1,1], combinatoric (16! leaves)", "perm_combinatoric", A16,
+              dict(max_terms=1 << 46), 20922789888000, 1),
+             ("32x32 complex128 Gaussian / sqrt(2n), Glynn", "perm_glynn", inputs.square32_c128(), None, 1 << 31,
+              reps),
+             ("20x40 float64 uniform[0,1], Glynn (padding in closed form: 2^19 sign vectors)", "perm_glynn", R, None,
+              1 << 19, reps),
+             ("20x40 float64 uniform[0,1], Ryser (2^40 subsets, 6.19e11 of size <= 20)", "perm_ryser", R, None,
+              1 << 40, 1),
+             ("26x26 0/1 Bernoulli(0.5), exact, Glynn", "perm_glynn", inputs.square26_01(), None, 1 << 25, reps)]
     res = {}
-    for name, A, terms in cases:
+    for name, fn, A, opts, terms, nrep in cases:
         dA = torch.from_numpy(A).to(dev)
         out = torch.empty(2 if A.dtype.kind in "ciu" else 1, dtype=torch.float64 if A.dtype.kind != "u" else
                           torch.int64, device=dev)
+        err = torch.empty(1, dtype=torch.float64, device=dev)
         with torch.cuda.stream(stream):
-            capi.perm_glynn(dA, out=out, stream=stream)
             best = float("inf")
-            for _ in range(reps):
+            if nrep > 1:
+                getattr(capi, fn)(dA, out=out, stream=stream, opts=opts)
+            for _ in range(nrep):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                capi.perm_glynn(dA, out=out, stream=stream)
+                getattr(capi, fn)(dA, out=out, stream=stream, opts=opts)
                 e1.record(stream)
                 e1.synchronize()
                 best = min(best, e0.elapsed_time(e1))
-        res[name] = {"ms": best, "terms_per_s": terms / (best * 1e-3)}
+        row = {"ms": best, "terms_per_s": terms / (best * 1e-3)}
+        if A.dtype.kind == "f" and fn != "perm_combinatoric":
+            o = dict(opts or {}, err=err)
+            getattr(capi, fn)(dA, out=out, stream=stream, opts=o)
+            stream.synchronize()
+            row["result"], row["err_bound"] = float(out[0].item()), float(err.item())
+        elif fn == "perm_combinatoric":
+            row["result"] = float(out[0].item())
+        res[name] = row
     return res
 
 
@@ -497,6 +594,7 @@ def run_ours(args):
             capi.perm_glynn(dA, out=out, stream=stream, opts=opts)
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
+    clock_summary = clocks.summary()
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -525,22 +623,32 @@ def run_ours(args):
         fixed = args.arith in ("fixed", "mixed")
     mixed = fixed and args.arith in ("auto", "mixed")
     launches_per_step = 3 if fixed else 2  # [fixed-point table,] sweep, final reduction
+    props = torch.cuda.get_device_properties(dev)
     if fixed:
-        roof = {"bound": "alu", "pipe": ("integer (ALU + IMAD) with a share of each product on the FP64 unit"
-                                         if mixed else "integer (ALU + IMAD); FP64 pipe idle"),
-                "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak_flops, "traffic": None,
-                "peak_source": "measured now: 2 x DFMA issue rate (perm_probe_rate); achieved counts the "
-                               "FP64-equivalent 2n operations per term, computed on the integer pipes",
-                "flops_per_term": flops_per_term}
-        if mixed and n in (33, 34, 35, 36) and args.dtype == "f64":
-            # pipe utilisation of this kernel (N = 36 columns, 8 on the FP64 unit) from one ncu
-            # capture at n = 34; DRAM traffic does not grow with the term count
-            roof["traffic"] = 562688
-            roof["traffic_source"] = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum of "
-                                      "glynn_fx_kernel<36, 8, 0> at n = 34 (profiles/glynn_fx_n36_launches.md)")
-            roof["pipes_ncu"] = {"alu": 0.628, "fp64": 0.614, "fma": 0.276, "issue": 0.573,
-                                 "source": "profiles/glynn_fx_mixed_n34_ncu.md"}
+        # The integer-pipe sweep is bound by instruction issue (ncu: issue ahead of every
+        # pipe).  Peak: one warp instruction per scheduler per clock, 4 schedulers per SM,
+        # at the maximum SM clock; achieved: thread instructions per term (ncu, below)
+        # times terms/s.
+        sm_max = (clock_summary or {}).get("sm_max_mhz") or 2070.0
+        issue_peak = props.multi_processor_count * 4 * 32 * sm_max * 1e6
+        prof = ISSUE_PROFILE.get((n + 3) & ~3) if (mixed and args.dtype == "f64") else None
+        roof = {"bound": "alu", "pipe": "instruction issue (integer ALU + IMAD, a share of each product on the "
+                                        "FP64 unit)" if mixed else "instruction issue (integer ALU + IMAD)",
+                "achieved": None, "peak": issue_peak / 1e12, "unit": "T thread-instructions/s", "frac": None,
+                "traffic": None,
+                "peak_source": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz (maximum SM clock)" % (
+                    props.multi_processor_count, sm_max)}
+        if prof:
+            ipt = prof["instructions_per_term"]
+            roof["achieved"] = ipt * terms / (ms_per_step * 1e-3) / 1e12
+            roof["frac"] = roof["achieved"] * 1e12 / issue_peak
+            roof["instructions_per_term"] = ipt
+            roof["traffic"] = prof["dram_bytes_per_launch"]
+            roof["pipes_ncu"] = prof["pipes"]
+            roof["evidence"] = prof["label"]
+        roof["fp64_equivalent"] = {"achieved_tflops": achieved / 1e12, "fp64_peak_tflops": peak_flops / 1e12,
+                                   "ratio": achieved / peak_flops, "flops_per_term": flops_per_term,
+                                   "peak_source": "measured now: 2 x DFMA issue rate (perm_probe_rate)"}
     else:
         roof = {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e12, "peak": peak_flops / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_flops, "traffic": None,
@@ -564,7 +672,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.nbytes),
                 "d2h_bytes_per_step": 8 * out.numel()},
         "gpu_launches": launches_per_step * args.steps,
-        "clocks": clocks.summary(),
+        "clocks": clock_summary,
     }
     if args.dtype == "c128":
         line["dtype"] = "c128"
@@ -601,6 +709,8 @@ def run_ours(args):
         line["precision"] = run_precision(dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if "batched" in line and BATCH_CHECK:
+            line["batched"]["accuracy"] = batched_oracle_check()
         cores = os.cpu_count() or 1
         rate, tt, wall = cpu_oracle_rate(A, args.cpu_seconds, cores)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

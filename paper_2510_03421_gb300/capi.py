@@ -8,6 +8,11 @@ through ``perm_glynn_gaussian`` and ``perm_batched_gaussian``) and accept torch
 tensors (CUDA or CPU) or numpy arrays; CPU / numpy buffers are passed as host
 pointers and the library copies them itself.  If the shared library has not been
 built this module raises -- there is no fallback.
+
+Streams: a call given ``stream=`` launches on that stream, and an ``out`` tensor the
+binding allocates belongs to that stream too.  The results are written asynchronously:
+synchronise that stream (or make the reading stream wait on it) before reading ``out``
+from another stream, e.g. with ``.item()`` or ``.cpu()`` on the current one.
 """
 from __future__ import annotations
 
@@ -156,13 +161,37 @@ def _matrix(A):
     return A, A.ctypes.data, m, n, n, dtype_code(A), None
 
 
-def _out_like(code: int, device, count: int = 1):
-    shape = (count,) if code == PERM_F64 else (count, 2)
+def _on_stream(device, stream):
+    """Context in which torch allocates on the stream the call launches on, so that the
+    caching allocator does not hand the block to other work while the call still runs."""
+    import contextlib
+    if device is None or stream is None:
+        return contextlib.nullcontext()
+    import torch
+    s = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(
+        stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream), device=device)
+    return torch.cuda.stream(s)
+
+
+def _empty(shape, floating: bool, device, stream=None):
     if device is not None:
         import torch
-        tdt = torch.float64 if code in (PERM_F64, PERM_C128) else torch.int64
-        return torch.empty(shape, dtype=tdt, device=device)
-    return np.empty(shape, dtype=np.float64 if code in (PERM_F64, PERM_C128) else np.int64)
+        with _on_stream(device, stream):
+            return torch.empty(shape, dtype=torch.float64 if floating else torch.int64, device=device)
+    return np.empty(shape, dtype=np.float64 if floating else np.int64)
+
+
+def _zeros(shape, device, stream=None):
+    if device is not None:
+        import torch
+        with _on_stream(device, stream):
+            return torch.zeros(shape, dtype=torch.int64, device=device)
+    return np.zeros(shape, dtype=np.int64)
+
+
+def _out_like(code: int, device, count: int = 1, stream=None):
+    shape = (count,) if code == PERM_F64 else (count, 2)
+    return _empty(shape, code in (PERM_F64, PERM_C128), device, stream)
 
 
 def _ptr(x) -> int:
@@ -198,7 +227,7 @@ def _device_index(device):
 def _call(name, A, out, stream, opts):
     keep, p, m, n, ld, code, dev = _matrix(A)
     if out is None:
-        out = _out_like(code, dev)
+        out = _out_like(code, dev, stream=stream)
     rc = getattr(lib(), name)(handle(_device_index(dev)), p, m, n, ld, code, _ptr(out), _stream(dev, stream),
                               _opts(opts))
     if rc:
@@ -231,12 +260,7 @@ def perm_glynn_partial(A, g_begin: int, g_end: int, out=None, stream=None, opts=
     keep, p, m, n, ld, code, dev = _matrix(A)
     if out is None:
         words = {PERM_F64: 2, PERM_C128: 4}.get(code, 2)
-        if dev is not None:
-            import torch
-            out = torch.empty(words, dtype=torch.float64 if code in (PERM_F64, PERM_C128) else torch.int64,
-                              device=dev)
-        else:
-            out = np.empty(words, dtype=np.float64 if code in (PERM_F64, PERM_C128) else np.int64)
+        out = _empty(words, code in (PERM_F64, PERM_C128), dev, stream)
     rc = lib().perm_glynn_partial(handle(_device_index(dev)), p, m, n, ld, code, g_begin, g_end, _ptr(out),
                                   _stream(dev, stream), _opts(opts))
     if rc:
@@ -248,11 +272,7 @@ def perm_ryser_partial(A, g_begin: int, g_end: int, out=None, stream=None, opts=
     """Weighted Ryser sum over the Gray-ordered subsets [g_begin, g_end) (double-double)."""
     keep, p, m, n, ld, code, dev = _matrix(A)
     if out is None:
-        if dev is not None:
-            import torch
-            out = torch.empty(2, dtype=torch.float64, device=dev)
-        else:
-            out = np.empty(2, dtype=np.float64)
+        out = _empty(2, True, dev, stream)
     rc = lib().perm_ryser_partial(handle(_device_index(dev)), p, m, n, ld, code, g_begin, g_end, _ptr(out),
                                   _stream(dev, stream), _opts(opts))
     if rc:
@@ -266,7 +286,7 @@ def perm_batched(packed, offsets, M, N, out=None, stream=None, opts=None):
     dev = packed.device if _is_torch(packed) and packed.is_cuda else None
     count = len(offsets)
     if out is None:
-        out = _out_like(code, dev, count)
+        out = _out_like(code, dev, count, stream)
     rc = lib().perm_batched(handle(_device_index(dev)), _ptr(packed), _ptr(offsets), _ptr(M), _ptr(N), count, code,
                             _ptr(out), _stream(dev, stream), _opts(opts))
     if rc:
@@ -280,7 +300,7 @@ def perm_sbp(C, occ, out=None, stream=None, opts=None):
     keep, p, n, N, ld, code, dev = _matrix(C)
     count = len(occ)
     if out is None:
-        out = _out_like(code, dev, count)
+        out = _out_like(code, dev, count, stream)
     rc = lib().perm_sbp(handle(_device_index(dev)), p, n, N, ld, code, _ptr(occ), count, _ptr(out),
                         _stream(dev, stream), _opts(opts))
     if rc:
@@ -306,7 +326,7 @@ def perm_cauchy(x, y, out=None, stream=None, opts=None):
         n = x.shape[-1]
         count = x.size // n if n else 0
     if out is None:
-        out = _out_like(PERM_F64, dev, count)
+        out = _out_like(PERM_F64, dev, count, stream)
     rc = lib().perm_cauchy(handle(_device_index(dev)), _ptr(x), _ptr(y), n, count, _ptr(out),
                            _stream(dev, stream), _opts(opts))
     if rc:
@@ -323,7 +343,7 @@ def perm_cauchy_sbp(x, y, occ, out=None, stream=None, opts=None):
         y = np.ascontiguousarray(y, dtype=np.float64)
     count = len(occ)
     if out is None:
-        out = _out_like(PERM_F64, dev, count)
+        out = _out_like(PERM_F64, dev, count, stream)
     rc = lib().perm_cauchy_sbp(handle(_device_index(dev)), _ptr(x), x.shape[-1], _ptr(y), y.shape[-1], _ptr(occ),
                                count, _ptr(out), _stream(dev, stream), _opts(opts))
     if rc:
@@ -343,11 +363,8 @@ def _gaussian(re, im):
     return G, G.ctypes.data, G.shape[0], G.shape[1], G.shape[1], None
 
 
-def _gaussian_out(dev):
-    if dev is not None:
-        import torch
-        return torch.zeros(4, dtype=torch.int64, device=dev)
-    return np.zeros(4, dtype=np.int64)
+def _gaussian_out(dev, stream=None):
+    return _zeros(4, dev, stream)
 
 
 def perm_batched_gaussian(packed, offsets, M, N, out=None, stream=None):
@@ -357,11 +374,7 @@ def perm_batched_gaussian(packed, offsets, M, N, out=None, stream=None):
     dev = packed.device if _is_torch(packed) and packed.is_cuda else None
     count = len(offsets)
     if out is None:
-        if dev is not None:
-            import torch
-            out = torch.zeros((count, 4), dtype=torch.int64, device=dev)
-        else:
-            out = np.zeros((count, 4), dtype=np.int64)
+        out = _zeros((count, 4), dev, stream)
     rc = lib().perm_batched(handle(_device_index(dev)), _ptr(packed), _ptr(offsets), _ptr(M), _ptr(N), count,
                             PERM_CI64, _ptr(out), _stream(dev, stream), None)
     if rc:
@@ -374,7 +387,7 @@ def perm_glynn_gaussian(re, im, out=None, stream=None, opts=None):
     two int128 (real, imaginary); read it with value(out, PERM_CI64)."""
     keep, p, m, n, ld, dev = _gaussian(re, im)
     if out is None:
-        out = _gaussian_out(dev)
+        out = _gaussian_out(dev, stream)
     rc = lib().perm_glynn(handle(_device_index(dev)), p, m, n, ld, PERM_CI64, _ptr(out), _stream(dev, stream),
                           _opts(opts))
     if rc:
@@ -386,7 +399,7 @@ def perm_glynn_partial_gaussian(re, im, g_begin: int, g_end: int, out=None, stre
     """Unnormalised Glynn sum of re + i im over terms [g_begin, g_end), modulo 2^128."""
     keep, p, m, n, ld, dev = _gaussian(re, im)
     if out is None:
-        out = _gaussian_out(dev)
+        out = _gaussian_out(dev, stream)
     rc = lib().perm_glynn_partial(handle(_device_index(dev)), p, m, n, ld, PERM_CI64, g_begin, g_end, _ptr(out),
                                   _stream(dev, stream), _opts(opts))
     if rc:
@@ -401,7 +414,7 @@ def perm_glynn_noalloc(A, out=None, stream=None, grid: int = 0):
     if code != PERM_F64 or dev is None:
         raise TypeError("perm_glynn_noalloc takes a float64 CUDA tensor")
     if out is None:
-        out = _out_like(code, dev)
+        out = _out_like(code, dev, stream=stream)
     rc = lib().perm_glynn_noalloc(p, m, n, ld, _ptr(out), _stream(dev, stream), grid)
     if rc:
         raise PermError(rc, "perm_glynn_noalloc")
@@ -430,7 +443,8 @@ def perm_mlp_forward(weights, dims, X, Y=None, stream=None):
     import torch
     in_dim, hid, out_dim = dims
     if Y is None:
-        Y = torch.empty((X.shape[0], out_dim), dtype=torch.float32, device=X.device)
+        with _on_stream(X.device, stream):
+            Y = torch.empty((X.shape[0], out_dim), dtype=torch.float32, device=X.device)
     _check(lib().perm_mlp_forward(weights.data_ptr(), in_dim, hid, out_dim, X.data_ptr(), X.shape[0], Y.data_ptr(),
                                   _stream(X.device, stream)), "perm_mlp_forward")
     return Y
@@ -440,8 +454,9 @@ def perm_mlp_grad(weights, dims, X, T, mask, stream=None):
     """(gradient, loss) of the masked MSE with respect to the flat weights (CUDA tensors)."""
     import torch
     in_dim, hid, out_dim = dims
-    grad = torch.empty_like(weights)
-    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    with _on_stream(X.device, stream):
+        grad = torch.empty_like(weights)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
     _check(lib().perm_mlp_grad(weights.data_ptr(), in_dim, hid, out_dim, X.data_ptr(), T.data_ptr(), mask.data_ptr(),
                                X.shape[0], grad.data_ptr(), loss.data_ptr(), _stream(X.device, stream)),
            "perm_mlp_grad")
@@ -452,8 +467,9 @@ def perm_mlp_train(X, T, mask, dims, epochs: int, batch: int, lr: float, seed: i
     """Train on the GPU; returns (weights, per-epoch loss) as CUDA tensors."""
     import torch
     in_dim, hid, out_dim = dims
-    weights = torch.empty(perm_mlp_size(in_dim, hid, out_dim), dtype=torch.float32, device=X.device)
-    hist = torch.zeros(max(epochs, 1), dtype=torch.float32, device=X.device)
+    with _on_stream(X.device, stream):
+        weights = torch.empty(perm_mlp_size(in_dim, hid, out_dim), dtype=torch.float32, device=X.device)
+        hist = torch.zeros(max(epochs, 1), dtype=torch.float32, device=X.device)
     _check(lib().perm_mlp_train(X.data_ptr(), T.data_ptr(), mask.data_ptr(), X.shape[0], in_dim, hid, out_dim, epochs,
                                 batch, lr, seed, weights.data_ptr(), hist.data_ptr(), _stream(X.device, stream)),
            "perm_mlp_train")

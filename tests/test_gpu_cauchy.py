@@ -299,3 +299,20 @@ def test_cauchy_sbp_bad_bitstrings_and_limits(capi, dev):
     with pytest.raises(capi.PermError) as e:
         capi.perm_cauchy_sbp(x, np.zeros(65), np.array([3], dtype=np.uint64))
     assert e.value.status == capi.PERM_ETOOBIG
+
+
+def test_side_stream_result_read_after_that_stream(capi, dev):
+    # a call on a side stream writes its result on that stream; after that stream is
+    # synchronised the value read equals the exact Borchardt value of the same points
+    import torch
+    side = torch.cuda.Stream(device=dev)
+    for n in (8, 12, 16):
+        x, y = inputs.cauchy_points(n, inputs.SEED_BASE + 20 + n, draws=100)
+        dx, dy = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+        torch.cuda.synchronize(dev)
+        out = capi.perm_cauchy(dx, dy, stream=side)
+        side.synchronize()
+        got = float(out[0].item())
+        exact = float(oracle.cauchy.permanent_borchardt(x[0], y[0]))
+        assert got > 0.0
+        assert abs(got - exact) <= 2.0 ** -52 * abs(exact), (n, got, exact)

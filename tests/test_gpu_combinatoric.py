@@ -1,11 +1,14 @@
-"""Parity of the combinatoric algorithm (perm_combinatoric) with the CPU oracle."""
+"""Parity of the combinatoric algorithm (perm_combinatoric) with the CPU oracle.
+
+Float tolerance: 8 (n + 2) u per(|A|), the sum of |term| of the definition's terms
+(gpu_util.close with kind="definition"); integers bit-exact."""
 import math
 
 import numpy as np
 import pytest
 
 import oracle
-from gpu_util import close, device, run
+from gpu_util import close, device, read_golden, run, to_dev
 from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -25,26 +28,26 @@ def capi():
 @pytest.mark.parametrize("m,n", [(1, 1), (1, 6), (2, 2), (3, 3), (4, 6), (5, 5), (6, 9), (8, 8), (9, 9)])
 def test_dense_real_vs_definition(capi, dev, m, n):
     A = inputs.uniform_real(m, n, 8000 + 31 * m + n)
-    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A), A)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A), A, kind="definition")
 
 
 def test_dense_real_12(capi, dev):
     A = inputs.uniform_real(12, 12, 8101)
-    close(run(capi, "perm_combinatoric", A, dev), oracle.glynn(A), A)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.glynn(A), A, kind="definition")
 
 
 @pytest.mark.parametrize("density", [0.15, 0.3])
 def test_sparse_real_16(capi, dev, density):
     # the work cap counts dense leaves (16!); a sparse input is pruned, so raise it
     A = inputs.sparse_real(16, 16, density, 8200 + int(100 * density))
-    close(run(capi, "perm_combinatoric", A, dev, dict(max_terms=1 << 62)), oracle.glynn(A), A)
+    close(run(capi, "perm_combinatoric", A, dev, dict(max_terms=1 << 62)), oracle.glynn(A), A, kind="definition")
 
 
 def test_transposed_and_complex(capi, dev):
     A = inputs.uniform_real(7, 4, 8301)
-    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A.T), A)
+    close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A.T), A, kind="definition")
     C = inputs.complex_gaussian(7, 7, 8302)
-    close(run(capi, "perm_combinatoric", C, dev), oracle.definition(C), C)
+    close(run(capi, "perm_combinatoric", C, dev), oracle.definition(C), C, kind="definition")
 
 
 @pytest.mark.parametrize("n", [3, 7, 10])
@@ -68,3 +71,18 @@ def test_work_cap(capi, dev):
     with pytest.raises(capi.PermError) as e:
         capi.perm_combinatoric(A)
     assert e.value.status == capi.PERM_ETOOBIG
+
+
+def test_config_square16_dense(capi, dev):
+    # the 16 x 16 uniform[-1,1] workload by the combinatoric algorithm: 16! injective
+    # maps (the default work cap of 2^44 leaves refuses it; the cap is raised for it),
+    # against the stored long-double Glynn and Ryser values of the same matrix
+    g = read_golden("square16_f64.txt")
+    A = inputs.square16_f64(int(g["seed"][0]))
+    ref = float(g["glynn"][0]) + float(g["glynn"][1])
+    assert abs(ref - (float(g["ryser"][0]) + float(g["ryser"][1]))) <= 1e-14 * abs(ref)
+    with pytest.raises(capi.PermError) as e:
+        capi.perm_combinatoric(to_dev(A, dev))
+    assert e.value.status == capi.PERM_ETOOBIG
+    got = run(capi, "perm_combinatoric", A, dev, dict(max_terms=1 << 46))
+    close(got, ref, A, kind="definition")

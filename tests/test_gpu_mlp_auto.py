@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import close, device, run, to_dev
+from gpu_util import auto_scale, close, device, run, to_dev
 from oracle import mlp_ref
 from paper_2510_03421_gb300 import inputs
 
@@ -88,12 +88,15 @@ def test_auto_results_match_oracle(capi, dev, kind):
         if kind == "u8":
             assert got == oracle.subset_dp(A.astype(np.int64))
         else:
-            close(got, oracle.glynn(A), A)
+            ref = oracle.glynn(A)
+            s, u = auto_scale(capi, A, dev)
+            close(got, ref, A, s=s, u=u)
         got_x = run(capi, "perm_auto", A, dev, dict(exhaustive=1))
         if kind == "u8":
             assert got_x == got
         else:
-            close(got_x, oracle.glynn(A), A)
+            s, u = auto_scale(capi, A, dev, exhaustive=True)
+            close(got_x, ref, A, s=s, u=u)
 
 
 def test_builtin_choice_without_model(capi, dev):
@@ -138,7 +141,8 @@ def test_model_installs_and_drives_perm_auto(capi, dev):
     for A in (inputs.uniform_real(4, 4, 1), inputs.uniform_real(18, 18, 2), inputs.sparse_real(14, 14, 0.1, 3)):
         c, pred = capi.perm_auto_choice(to_dev(A, dev))
         assert 0 <= c < capi.PERM_NCAND and np.isfinite(pred[c]) and pred[c] == np.min(pred)
-        close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A)
+        s, u = auto_scale(capi, A, dev)
+        close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A, s=s, u=u)
     capi.perm_set_cost_model(None, None)
 
 
@@ -158,6 +162,39 @@ def _block_matrix(g, shapes, complex_=False):
     return A[g.permutation(m)][:, g.permutation(n)]
 
 
+def _blockwise_scale(capi, dev, A):
+    """per(A) is the product of its blocks' permanents, each with a relative error of
+    c (n_k + 2) u scale_k / |per_k|: the product of the blocks' scales, times
+    sum_k (n_k + 2) / (n + 2), bounds the scale of the whole (blocks from the nonzero
+    pattern, each taken by the candidate perm_auto would choose for it)."""
+    rows, cols = np.nonzero(A)
+    m, n = A.shape
+    parent = list(range(m + n))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for i, j in zip(rows, cols):
+        parent[find(i)] = find(m + j)
+    groups = {}
+    for i in range(m):
+        groups.setdefault(find(i), ([], []))[0].append(i)
+    for j in range(n):
+        groups.setdefault(find(m + j), ([], []))[1].append(j)
+    prod, weight, umax = 1.0, 0.0, 0.0
+    for r, c in groups.values():
+        if not r:
+            continue
+        B = np.ascontiguousarray(A[np.ix_(r, c)])
+        s, u = auto_scale(capi, B, dev)
+        prod *= s
+        weight += max(len(r), len(c)) + 2
+        umax = max(umax, u)
+    return prod * weight / (max(m, n) + 2), umax
+
+
 @pytest.mark.parametrize("complex_", [False, True])
 def test_auto_splits_independent_blocks(capi, dev, complex_):
     # per(A) is the product of the blocks' permanents (each term keeps every row in its
@@ -165,8 +202,10 @@ def test_auto_splits_independent_blocks(capi, dev, complex_):
     g = inputs.rng(9960 + complex_)
     for shapes in ([(4, 4), (5, 5), (3, 3)], [(4, 6), (5, 5), (3, 4)], [(1, 1), (7, 9), (2, 2)]):
         A = _block_matrix(g, shapes, complex_)
-        close(run(capi, "perm_auto", A, dev), oracle.glynn(A), A)
-        close(run(capi, "perm_auto", np.ascontiguousarray(A.T), dev), oracle.glynn(A), A)
+        ref = oracle.glynn(A)
+        s, u = _blockwise_scale(capi, dev, A)
+        close(run(capi, "perm_auto", A, dev), ref, A, s=s, u=u)
+        close(run(capi, "perm_auto", np.ascontiguousarray(A.T), dev), ref, A, s=s, u=u)
 
 
 def test_auto_structural_zeros(capi, dev):

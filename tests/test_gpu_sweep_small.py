@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import U, device, run, term_bound
+from gpu_util import U, U_CFIX, device, run, scale
 from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -47,11 +47,11 @@ def test_random_small_shapes_all_entry_points(capi, dev, kind):
             A = np.ascontiguousarray(A.T)  # m > n: per(A^T)
         ref = oracle.definition(A)
         mm, nn = sorted(A.shape)
-        # first-order rounding scale of either formula: Glynn terms are bounded by the
-        # product of (padded) column sums, Ryser's 2^n terms by the product of row sums
-        B = A if A.shape[0] <= A.shape[1] else A.T
-        ryser_scale = 2.0 ** nn * float(np.prod(np.abs(B).sum(axis=1)))
-        tol = max(1e-12 * abs(ref), 8 * (nn + 2) * U * max(term_bound(A), ryser_scale))
+        # the largest sum of |term| over the term sets these entry points evaluate
+        # (Glynn padded or in closed form, Ryser, the definition)
+        if kind in ("f64", "c128"):
+            s = max(scale(A, k) for k in ("glynn", "esym", "ryser", "definition"))
+            tol = max(1e-12 * abs(ref), 8 * (nn + 2) * (U_CFIX if kind == "c128" else U) * s)
         for fn, opts in entry:
             got = run(capi, fn, A, dev, opts)
             if kind in ("u8", "i64"):
