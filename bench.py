@@ -485,6 +485,70 @@ def batched_oracle_check():
     return res
 
 
+CHUNK_STUDY = {}  # GPU partial sums kept for the oracle comparison of the CPU leg
+
+
+def run_chunk_start_study(dev, stream, span=4096, chunk_log2=6):
+    """GPU part of the chunk-start precision study on the 36x36 float64 and 32x32
+    complex128 workloads: term ranges at the start, middle and end of the Gray walk,
+    summed by each variant (FP64 with per-thread chunk starts, FP64 with the starts
+    from the tensor-core contraction, integer pipes, mixed); chunks of 2^6 terms, so
+    each range holds 64 chunk starts.  Also the whole 32x32 all-ones matrix (per =
+    32!, Eq. digits_lost) by each variant."""
+    import math
+
+    import torch
+
+    from paper_2510_03421_gb300 import capi, inputs
+    variants = {"fp64_thread_start": dict(arith=capi.PERM_ARITH_FP64, start=capi.PERM_START_SCALAR),
+                "fp64_tensor_core_start": dict(arith=capi.PERM_ARITH_FP64, start=capi.PERM_START_DMMA),
+                "integer_pipes": dict(arith=capi.PERM_ARITH_FIXED), "mixed": dict(arith=capi.PERM_ARITH_MIXED)}
+    cvariants = {"fp64": dict(arith=capi.PERM_ARITH_FP64), "integer_pipes": dict(arith=capi.PERM_ARITH_FIXED),
+                 "mixed": dict(arith=capi.PERM_ARITH_MIXED)}
+    out = {}
+    for wname, A, vs in (("36x36 float64", inputs.square36_f64(), variants),
+                         ("32x32 complex128", inputs.square32_c128(), cvariants)):
+        n = A.shape[0]
+        T = 1 << (n - 1)
+        ranges = [(0, span), (T // 3 + 77, T // 3 + 77 + span), (T - span, T)]
+        dA = torch.from_numpy(A).to(dev)
+        rows = {}
+        for vname, opts in vs.items():
+            vals = []
+            for a, b in ranges:
+                o = capi.perm_glynn_partial(dA, a, b, stream=stream, opts=dict(opts, chunk_log2=chunk_log2))
+                stream.synchronize()
+                v = o.cpu().numpy()
+                vals.append(float(v[0] + v[1]) if A.dtype.kind == "f" else complex(v[0] + v[1], v[2] + v[3]))
+            rows[vname] = vals
+        out[wname] = {"ranges": ranges, "values": rows}
+        CHUNK_STUDY[wname] = (A, ranges, rows)
+    ones = torch.ones((32, 32), dtype=torch.float64, device=dev)
+    exact = float(math.factorial(32))
+    eps = 2.0 ** -52
+    digits = {}
+    for vname, opts in variants.items():
+        r = capi.perm_glynn(ones, stream=stream, opts=opts)
+        stream.synchronize()
+        e = abs(float(r.item()) - exact)
+        digits[vname] = None if e == 0 else round(math.log10(e / exact) - math.log10(eps), 2)
+    return {"metric": "chunk-start variants: partial sums on sampled term ranges (errors against the "
+                      "long-double oracle in the CPU leg) and digits lost on the 32x32 all-ones matrix",
+            "chunk_log2": chunk_log2, "span": span, "ones_32x32_digits_lost": digits}
+
+
+def chunk_start_oracle_check():
+    """CPU leg: each variant's sampled-range partial sums against the oracle's, in units
+    of the range's sum of |term| (the scale of any evaluation's rounding)."""
+    import oracle
+    res = {}
+    for wname, (A, ranges, rows) in CHUNK_STUDY.items():
+        truth = [oracle.glynn_partial(A, a, b) for a, b in ranges]
+        scale = [oracle.glynn_partial_abs(A, a, b) for a, b in ranges]
+        res[wname] = {v: max(abs(x - t) / s for x, t, s in zip(vals, truth, scale)) for v, vals in rows.items()}
+    return {"max_error_over_sum_abs": res}
+
+
 # ----------------------------------------------------------------------------- other configs
 def run_configs(dev, stream, reps=3):
     """Time each of the other workloads (CUDA events, best of `reps` after a warm-up):
@@ -707,10 +771,13 @@ def run_ours(args):
         line["batched_int"] = run_batched_int(args, dev, side)
         line["cauchy"] = run_cauchy(args, dev, side)
         line["precision"] = run_precision(dev, side)
+        line["precision"]["chunk_start"] = run_chunk_start_study(dev, side)
         line["other_configs"] = run_configs(dev, side)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if "batched" in line and BATCH_CHECK:
             line["batched"]["accuracy"] = batched_oracle_check()
+        if CHUNK_STUDY:
+            line["precision"]["chunk_start"].update(chunk_start_oracle_check())
         cores = os.cpu_count() or 1
         rate, tt, wall = cpu_oracle_rate(A, args.cpu_seconds, cores)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -24,13 +24,22 @@
 extern "C" {
 #endif
 
-/* Candidates perm_auto chooses between (output index of the cost model). */
+/* Candidates perm_auto chooses between (output index of the cost model): an algorithm
+ * with a kernel configuration (arithmetic, how chunk starts are formed, chunk length). */
 typedef enum {
   PERM_CAND_COMBINATORIC = 0, /* perm_combinatoric */
-  PERM_CAND_RYSER = 1,        /* perm_ryser (real input) */
-  PERM_CAND_GLYNN = 2,        /* perm_glynn, FP64 / exact integer arithmetic */
-  PERM_CAND_GLYNN_FIXED = 3,  /* perm_glynn with PERM_ARITH_FIXED (real input) */
-  PERM_NCAND = 4,
+  PERM_CAND_RYSER = 1,        /* perm_ryser, default arithmetic (real: integer pipes from n = 10 or the
+                                 by-size walk; complex FP64; integers exact) */
+  PERM_CAND_GLYNN = 2,        /* perm_glynn, FP64 (real), default (complex), exact (integers) */
+  PERM_CAND_GLYNN_FIXED = 3,  /* perm_glynn, PERM_ARITH_MIXED: integer pipes with a share of each product
+                                 on the FP64 unit (real input) */
+  PERM_CAND_RYSER_FP64 = 4,   /* perm_ryser, PERM_ARITH_FP64 (real input) */
+  PERM_CAND_GLYNN_DMMA = 5,   /* perm_glynn, PERM_ARITH_FP64 with chunk starts from the FP64 tensor-core
+                                 contraction (real input, n <= 48) */
+  PERM_CAND_GLYNN_INT = 6,    /* perm_glynn, PERM_ARITH_FIXED: integer pipes only (real input) */
+  PERM_CAND_GLYNN_SHORT = 7,  /* perm_glynn, PERM_ARITH_MIXED with chunks of 2^6 terms (real), or
+                                 PERM_ARITH_FP64 (complex) */
+  PERM_NCAND = 8,
   PERM_CAND_CAUCHY = 8        /* not a cost-model output: a real square matrix of order >= 24 whose
                                  entries are 1/(x_i - y_j) within 2^-48 relative, all of one sign,
                                  is evaluated by Borchardt's theorem on the fitted points (see

@@ -72,6 +72,7 @@ def _load():
                 getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec).argtypes = [i, i, p, i64, p]
                 getattr(lib, "oracle_glynn_esym_abs_%s" % prec).argtypes = [i, i, p, i64, p]
                 getattr(lib, "oracle_glynn_esym_abs_c_%s" % prec).argtypes = [i, i, p, i64, p]
+                getattr(lib, "oracle_glynn_rect_grouped_abs_c_%s" % prec).argtypes = [i, i, p, i64, p]
                 getattr(lib, "oracle_ryser_rect_abs_%s" % prec).argtypes = [i, i, p, i64, p]
             for name in ("oracle_definition_i128", "oracle_glynn_i128", "oracle_ryser_rect_i128"):
                 getattr(lib, name).argtypes = [i, i, p, i64, p]
@@ -225,15 +226,16 @@ def glynn_rect_grouped(A, prec: str = "ld", dd: bool = False):
 
 def glynn_rect_grouped_abs(A, prec: str = "ld") -> float:
     """Sum of |term| over all 2^(n-1) terms of Eq. glynn_rectangle (unnormalised), evaluated
-    by the grouping of glynn_rect_grouped.  Real input."""
+    by the grouping of glynn_rect_grouped.  Real or complex input (complex by modulus)."""
     lib = _load()
     A, kind, m, n = _prepare(A)
-    if kind != "real":
-        raise TypeError("glynn_rect_grouped_abs takes a real matrix")
+    if kind == "int":
+        raise TypeError("glynn_rect_grouped_abs takes a real or complex matrix")
     if m == 0:
         return 1.0
     out = (ctypes.c_double * 2)()
-    getattr(lib, "oracle_glynn_rect_grouped_abs_%s" % prec)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, out)
+    fn = "oracle_glynn_rect_grouped_abs_%s%s" % ("c_" if kind == "complex" else "", prec)
+    getattr(lib, fn)(m, n, A.ctypes.data_as(ctypes.c_void_p), n, out)
     return float(out[0]) + float(out[1])
 
 

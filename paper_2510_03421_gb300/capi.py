@@ -35,8 +35,9 @@ EXPORTS = ("perm_create", "perm_destroy", "perm_glynn", "perm_ryser", "perm_comb
            "perm_auto_features", "perm_mlp_size", "perm_mlp_forward", "perm_mlp_grad", "perm_mlp_train",
            "perm_set_cost_model", "perm_auto_choice", "perm_ryser_partial", "perm_sbp", "perm_cauchy",
            "perm_cauchy_sbp")
-PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED = range(4)
-PERM_NCAND = 4
+(PERM_CAND_COMBINATORIC, PERM_CAND_RYSER, PERM_CAND_GLYNN, PERM_CAND_GLYNN_FIXED, PERM_CAND_RYSER_FP64,
+ PERM_CAND_GLYNN_DMMA, PERM_CAND_GLYNN_INT, PERM_CAND_GLYNN_SHORT) = range(8)
+PERM_NCAND = 8
 PERM_CAND_CAUCHY = 8
 PERM_NFEATURES = 12
 PROBE_DFMA, PROBE_DMMA, PROBE_IMAD, PROBE_IADD, PROBE_FFMA = range(5)

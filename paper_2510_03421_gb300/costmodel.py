@@ -3,9 +3,11 @@ trained on the GPU by the library's own MLP kernels, and its evaluation.
 
 The paper tunes two linear hyperplanes in (m/n, n) at build time (Algorithm
 "Optimized Algorithm Selection", p1..p8).  Here a small perceptron predicts
-log2(seconds) of every candidate from features of the matrix (order, shape,
-density, dtype, log work counts; ``capi.perm_auto_features``) and perm_auto runs
-the argmin.  This module:
+log2(seconds) of every candidate -- an algorithm together with a kernel configuration
+(arithmetic: FP64, integer pipes, mixed; chunk starts per thread or from the FP64
+tensor-core contraction; chunk length) -- from features of the matrix (order, shape,
+density, dtype, log work counts; ``capi.perm_auto_features``) and perm_auto runs the
+argmin.  This module:
 
 * times candidates on a seeded grid of (m, n, density, dtype) cells
   (``measure_grid``), extrapolating sweeps too long to run from a timed term range;
@@ -14,7 +16,7 @@ the argmin.  This module:
 * refits the paper's rule (``PaperRule``) on the same timings as a baseline;
 * scores policies on a held-out batch against exhaustive timing (``evaluate``).
 
-Usage (on a GPU):  python -m paper_2510_03421_gb300.costmodel --cells 600 --eval 10000
+Usage (on a GPU):  python -m paper_2510_03421_gb300.costmodel --cells 3000 --eval 10000
 """
 from __future__ import annotations
 
@@ -28,17 +30,40 @@ import numpy as np
 
 from . import capi, inputs
 
-CANDS = ("combinatoric", "ryser", "glynn", "glynn_fixed")
+CANDS = ("combinatoric", "ryser", "glynn", "glynn_mixed", "ryser_fp64", "glynn_fp64_tensor_core_start",
+         "glynn_integer_only", "glynn_short_chunks_or_complex_fp64")
 DTYPES = {"f64": capi.PERM_F64, "c128": capi.PERM_C128, "u8": capi.PERM_U8}
 DIMS = (capi.PERM_NFEATURES, 64, capi.PERM_NCAND)
 MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "costmodel_gb300.npz")
 
-# candidates that exist per dtype
+# candidates that exist per dtype (shape limits are applied in time_candidate, as in
+# the library's own feasibility test)
 AVAILABLE = {
-    capi.PERM_F64: (True, True, True, True),
-    capi.PERM_C128: (True, False, True, False),
-    capi.PERM_U8: (True, False, True, False),
+    capi.PERM_F64: (True,) * 8,
+    capi.PERM_C128: (True, False, True, False, False, False, False, True),
+    capi.PERM_U8: (True, False, True, False, False, False, False, False),
 }
+
+
+def cand_opts(cand, code):
+    """(entry point, opts) perm_auto runs for candidate `cand` on dtype `code`."""
+    real = code == capi.PERM_F64
+    if cand == 1:
+        return "ryser", {}
+    if cand == 2:
+        return "glynn", dict(arith=capi.PERM_ARITH_FP64) if real else {}
+    if cand == 3:
+        return "glynn", dict(arith=capi.PERM_ARITH_MIXED)
+    if cand == 4:
+        return "ryser", dict(arith=capi.PERM_ARITH_FP64)
+    if cand == 5:
+        return "glynn", dict(arith=capi.PERM_ARITH_FP64, start=capi.PERM_START_DMMA)
+    if cand == 6:
+        return "glynn", dict(arith=capi.PERM_ARITH_FIXED)
+    if cand == 7:
+        return "glynn", dict(arith=capi.PERM_ARITH_MIXED, chunk_log2=6) if real else dict(arith=capi.PERM_ARITH_FP64)
+    raise ValueError(cand)
+
 
 BUDGET_S = 0.02        # longest run timed in full; longer ones are extrapolated
 TERM_SAMPLE = 1 << 22  # terms timed for an extrapolated sweep
@@ -60,13 +85,29 @@ def _log2_nodes(m, n, d):
     return math.log2(total) if total > 1 else 0.0
 
 
+def _esym(m, n):
+    """The integer pipes take a real rectangle with the padding in closed form (m n
+    multiply-adds per sign vector) when m <= 32 and n - m >= 3 or m <= 8."""
+    return m < n and m <= 32 and (n - m >= 3 or m <= 8)
+
+
+def _ryser_by_size(m, n):
+    if m >= n:
+        return None
+    by_size = sum(math.comb(n, s) for s in range(1, m + 1))
+    return by_size if 3 * by_size < (1 << n) else None
+
+
 def work_log2(m, n, density, cand):
     """log2 of the work count of a candidate (terms x width)."""
     if cand == 0:
         return _log2_nodes(m, n, max(density, 1e-3))
-    if cand == 1:
-        return n + math.log2(max(m, 1))
-    if cand == 3 and m < n:
+    if cand in (1, 4):
+        bs = _ryser_by_size(m, n)
+        return math.log2(bs) + math.log2(max(m, 1)) if bs else n + math.log2(max(m, 1))
+    if cand in (3, 6, 7) and m < n:
+        if _esym(m, n):
+            return (m - 1) + math.log2(m * n)
         return (m - 1) + math.log2(n - m + 1) + math.log2(n)
     return (n - 1) + math.log2(max(n, 1))
 
@@ -80,8 +121,9 @@ class Timer:
         self.e0 = torch.cuda.Event(enable_timing=True)
         self.e1 = torch.cuda.Event(enable_timing=True)
 
-    def run(self, fn, reps=2):
-        best = float("inf")
+    def run(self, fn, reps=3):
+        """Median of `reps` timed runs after a warm-up (robust to a stray slow run)."""
+        times = []
         with self.torch.cuda.stream(self.stream):
             fn()  # warm-up (and first-use setup)
             for _ in range(reps):
@@ -89,50 +131,55 @@ class Timer:
                 fn()
                 self.e1.record(self.stream)
                 self.e1.synchronize()
-                best = min(best, self.e0.elapsed_time(self.e1) * 1e-3)
-        return best
+                times.append(self.e0.elapsed_time(self.e1) * 1e-3)
+        return float(np.median(times))
 
 
-def time_candidate(timer, dA, m, n, density, code, cand):
+def time_candidate(timer, dA, m, n, density, code, cand, reps=3):
     """Seconds for candidate `cand` on the device matrix dA (m <= n), or None if the
-    candidate does not exist for the dtype.  Long sweeps are timed on a term range
-    and scaled; long combinatoric searches are scaled from the node count."""
+    candidate does not exist for the dtype and shape.  Long sweeps are timed on a term
+    range (squares) or a leading block of rows (rectangles) and scaled by the work
+    count; long combinatoric searches are labelled later from the node count."""
     if not AVAILABLE[code][cand]:
+        return None
+    if cand == 5 and (m != n or n > 48):
+        return None
+    if cand == 7 and code == capi.PERM_C128 and m != n:
         return None
     s = timer.stream
     big = dict(max_terms=1 << 62)
     if cand == 0:
-        lw = work_log2(m, n, density, 0)
-        if lw > 30:  # about a second or more: scale from a smaller search of the same density
+        if work_log2(m, n, density, 0) > 30:  # about a second or more
             return None
-        return timer.run(lambda: capi.perm_combinatoric(dA, stream=s, opts=big))
-    if cand == 1:
-        total = 1 << n
-        if total <= TERM_SAMPLE * 4:
-            return timer.run(lambda: capi.perm_ryser(dA, stream=s, opts=big))
-        if m > n:
-            return None
-        part = timer.run(lambda: capi.perm_ryser_partial(dA, 0, TERM_SAMPLE, stream=s, opts=big))
-        return part * total / TERM_SAMPLE
-    if cand == 3 and m < n:
-        # the integer-pipe candidate walks a rectangle grouped: 2^(m-1) (n-m+1) terms of
-        # n columns; a long walk is timed on its first mm rows and scaled by the terms
-        opts = dict(big, arith=capi.PERM_ARITH_MIXED)
-        steps = (1 << (m - 1)) * (n - m + 1)
-        if steps <= TERM_SAMPLE * 4:
-            return timer.run(lambda: capi.perm_glynn(dA, stream=s, opts=opts))
-        mm = m
-        while mm > 1 and (1 << (mm - 1)) * (n - mm + 1) > TERM_SAMPLE:
+        return timer.run(lambda: capi.perm_combinatoric(dA, stream=s, opts=big), reps)
+    fn, opts = cand_opts(cand, code)
+    opts = dict(big, **opts)
+    full = getattr(capi, "perm_" + fn)
+    lw = work_log2(m, n, density, cand)
+    if lw <= math.log2(TERM_SAMPLE) + 2 + math.log2(max(n, 1)):
+        return timer.run(lambda: full(dA, stream=s, opts=opts), reps)
+    if fn == "glynn" and m == n:
+        part = timer.run(lambda: capi.perm_glynn_partial(dA, 0, TERM_SAMPLE, stream=s, opts=opts), reps)
+        return part * (1 << (n - 1)) / TERM_SAMPLE
+    if fn == "ryser" and cand == 4 and _ryser_by_size(m, n) is None:
+        part = timer.run(lambda: capi.perm_ryser_partial(dA, 0, TERM_SAMPLE, stream=s, opts=opts), reps)
+        return part * (1 << n) / TERM_SAMPLE
+    # a smaller problem of the same kind: fewer rows (rectangular Glynn), or fewer
+    # columns (Ryser), scaled by the ratio of the work counts
+    mm, nn = m, n
+    while work_log2(mm, nn, density, cand) > math.log2(TERM_SAMPLE) + math.log2(max(nn, 1)):
+        if fn == "glynn" and mm > 1:
             mm -= 1
-        sub = dA[:mm]
-        part = timer.run(lambda: capi.perm_glynn(sub, stream=s, opts=opts))
-        return part * steps / ((1 << (mm - 1)) * (n - mm + 1))
-    opts = dict(big, arith=capi.PERM_ARITH_MIXED if cand == 3 else capi.PERM_ARITH_FP64)
-    total = 1 << (n - 1)
-    if total <= TERM_SAMPLE * 4:
-        return timer.run(lambda: capi.perm_glynn(dA, stream=s, opts=opts))
-    part = timer.run(lambda: capi.perm_glynn_partial(dA, 0, TERM_SAMPLE, stream=s, opts=opts))
-    return part * total / TERM_SAMPLE
+        elif nn > mm + 1:
+            nn -= 1
+        elif mm > 1:
+            mm -= 1
+            nn -= 1
+        else:
+            break
+    sub = dA[:mm, :nn]
+    part = timer.run(lambda: full(sub, stream=s, opts=opts), reps)
+    return part * 2.0 ** (lw - work_log2(mm, nn, density, cand))
 
 
 def grid_cells(count, seed):
@@ -269,20 +316,25 @@ class PaperRule:
         return 2 if p[4] * r + p[5] * n / 64 + p[6] > 0 else 1
 
 
-def evaluate(dev, weights, rule, count, seed, log=None, max_best_s=0.01):
-    """Held-out matrices from cells whose best time is at most max_best_s: time every
-    candidate (exhaustive), and score each policy by sum time(choice) / sum time(best)."""
+def evaluate(dev, weights, rule, count, seed, log=None, max_best_s=0.01, reps=3, max_n=24):
+    """Held-out matrices from cells whose best time is at most max_best_s (and n <=
+    max_n, so that timing every candidate stays cheap): time every candidate
+    (exhaustive, median of `reps`), and score each policy by sum time(choice) / sum
+    time(best), overall and per dtype."""
     import torch
     capi.perm_set_cost_model(None, None)  # perm_auto_choice then reports the built-in rule
     timer = Timer(dev)
     g = inputs.rng(seed)
     pairs = [(m, n) for m in range(2, 41) for n in range(m, 61)]
-    totals = {"best": 0.0, "model": 0.0, "paper_rule": 0.0, "always_glynn": 0.0, "builtin": 0.0}
+    policies = ("best", "model", "paper_rule", "always_glynn", "builtin")
+    totals = {p: 0.0 for p in policies}
+    per_dtype = {dt: {p: 0.0 for p in policies} for dt in DTYPES}
+    counts = {dt: 0 for dt in DTYPES}
     agree, k, tries = 0, 0, 0
     while k < count and tries < 20 * count:
         tries += 1
         m, n = pairs[int(g.integers(len(pairs)))]
-        if (1 << (n - 1)) > (1 << 24):  # keep exhaustive timing of every candidate cheap
+        if n > max_n:
             continue
         d = float(g.choice([0.1, 0.5, 1.0]))
         dt = str(g.choice(list(DTYPES)))
@@ -293,7 +345,7 @@ def evaluate(dev, weights, rule, count, seed, log=None, max_best_s=0.01):
         times = []
         for c in range(capi.PERM_NCAND):
             try:
-                s = time_candidate(timer, dA, m, n, nnz, code, c)
+                s = time_candidate(timer, dA, m, n, nnz, code, c, reps=reps)
             except capi.PermError:
                 s = None
             times.append(math.inf if s is None else s)
@@ -305,19 +357,25 @@ def evaluate(dev, weights, rule, count, seed, log=None, max_best_s=0.01):
         y = [y[c] if math.isfinite(times[c]) else math.inf for c in range(capi.PERM_NCAND)]
         choice = int(np.argmin(y))
         builtin, _ = capi.perm_auto_choice(dA)
-        totals["best"] += best
-        totals["builtin"] += times[builtin] if math.isfinite(times[builtin]) else times[2]
-        totals["model"] += times[choice]
-        totals["paper_rule"] += times[rule.choose(m, n, code)] if math.isfinite(times[rule.choose(m, n, code)]) \
-            else times[2]
-        totals["always_glynn"] += times[3] if code == capi.PERM_F64 else times[2]
+        pr = rule.choose(m, n, code)
+        row = {"best": best, "model": times[choice],
+               "builtin": times[builtin] if math.isfinite(times[builtin]) else times[2],
+               "paper_rule": times[pr] if math.isfinite(times[pr]) else times[2],
+               "always_glynn": times[3] if code == capi.PERM_F64 else times[2]}
+        for p in policies:
+            totals[p] += row[p]
+            per_dtype[dt][p] += row[p]
+        counts[dt] += 1
         agree += int(times[choice] == best)
         k += 1
         if log and k % 500 == 0:
             log("evaluated %d/%d" % (k, count))
     ratio = {p: totals[p] / totals["best"] for p in totals if p != "best"}
-    return {"matrices": k, "ratio_to_exhaustive": ratio, "model_picks_best": agree / max(k, 1),
-            "total_best_s": totals["best"]}
+    by_dtype = {dt: {p: per_dtype[dt][p] / per_dtype[dt]["best"] for p in policies if p != "best"}
+                for dt in DTYPES if counts[dt]}
+    return {"matrices": k, "per_dtype_matrices": counts, "ratio_to_exhaustive": ratio,
+            "ratio_to_exhaustive_by_dtype": by_dtype, "model_picks_best": agree / max(k, 1),
+            "total_best_s": totals["best"], "timing": "median of %d after a warm-up" % reps}
 
 
 def save(path, weights, meta):
@@ -351,7 +409,7 @@ def install(path=MODEL_PATH, device=0):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cells", type=int, default=600)
+    ap.add_argument("--cells", type=int, default=3000)
     ap.add_argument("--eval", type=int, default=10000)
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--out", default=MODEL_PATH)

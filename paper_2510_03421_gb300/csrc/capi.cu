@@ -244,7 +244,9 @@ int glynn_fp64(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   a.cs = c.cs;
   a.g_begin = g0;
   a.g_end = g1;
-  a.chunk_log2 = c.o.chunk_log2 ? c.o.chunk_log2 : 14;
+  // with an error bound: column sums rebuilt every 2^8 terms (the drift term of the
+  // bound grows with the chunk length; the rebuild costs n^2 / 2^8 per term)
+  a.chunk_log2 = c.o.chunk_log2 ? c.o.chunk_log2 : (want_abs ? 8 : 14);
   a.start_mode = c.o.start ? c.o.start : PERM_START_SCALAR;
   a.partials = partials_base(c.h);
   if (launch_glynn_f64(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
@@ -621,7 +623,7 @@ int ryser_real(Call& c, bool raw = false, uint64_t g0 = 0, uint64_t g1 = 0) {
   int bps = ryser_f64_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block, weighted, want_abs);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, terms, 16, (want_abs ? kCplxRecord : kRealRecord) * sizeof(double));
   lc.stream = c.stream;
-  SweepArgs a = sweep_args(c, g0, g1, 14);
+  SweepArgs a = sweep_args(c, g0, g1, want_abs ? 8 : 14);  // shorter chunks bound the drift tighter
   SizeWeights w;
   for (int s = 0; s <= 64; ++s) {
     w.w[s] = 0.0;
@@ -785,6 +787,12 @@ void feasible(int m, int n, double density, int dtype, uint64_t cap, bool* ok) {
   // rectangles: the grouped walk, 2^(m-1) (n-m+1) terms
   const double lfixed = m < n ? (double)(m - 1) + std::log2((double)(n - m + 1)) : (double)(n - 1);
   ok[PERM_CAND_GLYNN_FIXED] = dtype == PERM_F64 && lfixed <= lcap;
+  ok[PERM_CAND_RYSER_FP64] = ok[PERM_CAND_RYSER];
+  // the FP64 configurations evaluate the padded sum of a rectangle: squares only
+  ok[PERM_CAND_GLYNN_DMMA] = dtype == PERM_F64 && m == n && n <= glynn_dmma_max_n() && (double)(n - 1) <= lcap;
+  ok[PERM_CAND_GLYNN_INT] = ok[PERM_CAND_GLYNN_FIXED];
+  ok[PERM_CAND_GLYNN_SHORT] = (dtype == PERM_F64 && ok[PERM_CAND_GLYNN_FIXED]) ||
+                              (dtype == PERM_C128 && m == n && ok[PERM_CAND_GLYNN]);
 }
 
 // Host-side inference of the installed model.
@@ -942,6 +950,7 @@ int choose(perm_handle h, int m, int n, double density, int dtype, uint64_t cap,
     y[PERM_CAND_RYSER] = 3.f;
     y[PERM_CAND_GLYNN] = dtype == PERM_F64 ? 1.f : 0.f;
     y[PERM_CAND_GLYNN_FIXED] = 0.f;
+    for (int k = PERM_CAND_RYSER_FP64; k < PERM_NCAND; ++k) y[k] = 4.f;  // configurations of the above
   }
   int best = -1;
   for (int k = 0; k < PERM_NCAND; ++k) {
@@ -970,6 +979,27 @@ int run_candidate(Call& c, int cand) {
       return glynn_integer(c, false, 0, terms);
     }
     case PERM_CAND_GLYNN_FIXED: return glynn_fixed(c, false, 0, 1ull << (c.n - 1), true);
+    case PERM_CAND_RYSER_FP64: {
+      Call cc = c;
+      cc.o.arith = PERM_ARITH_FP64;
+      return ryser_real(cc);
+    }
+    case PERM_CAND_GLYNN_DMMA: {
+      Call cc = c;
+      cc.o.arith = PERM_ARITH_FP64;
+      cc.o.start = PERM_START_DMMA;
+      return glynn_fp64(cc, false, 0, 1ull << (c.n - 1));
+    }
+    case PERM_CAND_GLYNN_INT: return glynn_fixed(c, false, 0, 1ull << (c.n - 1), false);
+    case PERM_CAND_GLYNN_SHORT: {
+      Call cc = c;
+      if (c.dtype == PERM_C128) {
+        cc.o.arith = PERM_ARITH_FP64;
+        return glynn_cplx(cc, false, 0, 1ull << (c.n - 1));
+      }
+      cc.o.chunk_log2 = 6;
+      return glynn_fixed(cc, false, 0, 1ull << (c.n - 1), true);
+    }
     default: return PERM_EINVAL;
   }
 }

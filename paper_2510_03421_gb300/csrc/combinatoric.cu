@@ -319,7 +319,7 @@ int combinatoric_blocks_per_sm(int m, int n, int dtype, int block) {
   void* k = pick(dtype);
   if (!k) return 0;
   size_t smem = smem_bytes(m, n, dtype);
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (smem > 32 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
@@ -330,7 +330,7 @@ cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64
   void* k = pick(dtype);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.m, a.n, dtype);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -230,7 +230,7 @@ int glynn_cesym_blocks_per_sm(int m, int n, int block) {
   void* k = pick(m);
   if (!k || n > 64 || m >= n) return 0;
   const size_t smem = smem_bytes(m, n, block);
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (smem > 32 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
@@ -245,7 +245,7 @@ cudaError_t launch_glynn_cesym(const SweepArgs& a, CesymTable* tab, const Launch
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = smem_bytes(a.m, a.n, c.block);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

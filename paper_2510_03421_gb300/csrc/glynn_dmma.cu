@@ -158,7 +158,7 @@ int glynn_dmma_blocks_per_sm(int n, int block, bool want_abs) {
   void* k = pick(n, want_abs);
   if (!k) return 0;
   size_t smem = smem_bytes(n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -168,7 +168,7 @@ cudaError_t launch_glynn_dmma(const SweepArgs& a, const LaunchCfg& c, bool want_
   void* k = pick(a.n, want_abs);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

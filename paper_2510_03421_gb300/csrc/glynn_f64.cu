@@ -147,7 +147,7 @@ int glynn_f64_blocks_per_sm(int n, int block, bool want_abs) {
   void* k = pick(n, want_abs);
   if (!k) return 0;
   size_t smem = smem_bytes(n);
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (smem > 32 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -160,7 +160,7 @@ cudaError_t launch_glynn_f64(const SweepArgs& a, const LaunchCfg& c, bool want_a
   void* k = pick(a.n, want_abs);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -265,7 +265,7 @@ int glynn_fx_blocks_per_sm(int n, int block, bool mixed) {
   void* k = pick(n, mixed, false);
   if (!k) return 0;
   const size_t smem = smem_bytes(n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -282,7 +282,7 @@ cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c
   cudaError_t e = launch_fx_prep(a, tab, c.stream);
   if (e != cudaSuccess) return e;
   const size_t smem = smem_bytes(a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

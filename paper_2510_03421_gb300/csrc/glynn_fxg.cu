@@ -203,7 +203,7 @@ int glynn_fxg_blocks_per_sm(int m, int n, int block) {
   void* k = pick(n);
   if (!k) return 0;
   const size_t smem = smem_bytes(m, n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -216,7 +216,7 @@ cudaError_t launch_glynn_fxg(const SweepArgs& a, FxTable* tab, const LaunchCfg& 
   cudaError_t e = launch_fx_prep(a, tab, c.stream);
   if (e != cudaSuccess) return e;
   const size_t smem = smem_bytes(a.m, a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

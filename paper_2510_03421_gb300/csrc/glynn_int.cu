@@ -426,7 +426,7 @@ int glynn_int_blocks_per_sm(int n, int dtype, int block, bool grouped) {
   void* k = grouped ? pick_grouped(n, dtype) : pick(n, dtype);
   if (!k) return 0;
   size_t smem = smem_bytes(n);  // at least the grouped walk's (m + 1) rows
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -437,7 +437,7 @@ cudaError_t launch_glynn_int(const SweepArgs& a, int dtype, const LaunchCfg& c, 
   void* k = grouped ? pick_grouped(a.n, dtype) : pick(a.n, dtype);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = grouped ? 2u * (size_t)(a.m + 1) * (size_t)((a.n + 3) & ~3) * sizeof(long long) : smem_bytes(a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

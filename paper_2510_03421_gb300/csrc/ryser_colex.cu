@@ -159,7 +159,7 @@ int ryser_colex_blocks_per_sm(int m, int n, int block) {
   void* k = pick(m);
   if (!k) return 0;
   size_t smem = smem_bytes(m, n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -169,7 +169,7 @@ cudaError_t launch_ryser_colex(const SweepArgs& a, const SizeWeights& w, const S
   void* k = pick(a.m);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.m, a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -364,7 +364,7 @@ int ryser_ext_blocks_per_sm(int m, int n, int dtype, int block) {
   void* k = pick(m, dtype, m < n);
   if (!k) return 0;
   size_t smem = smem_bytes(m, n, dtype);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -375,7 +375,7 @@ cudaError_t launch_ryser_ext(const SweepArgs& a, int dtype, const SizeWeights& f
   void* k = pick(a.m, dtype, a.m < a.n);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.m, a.n, dtype);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

@@ -155,7 +155,7 @@ int ryser_f64_blocks_per_sm(int m, int n, int block, bool weighted, bool want_ab
   void* k = pick(m, weighted, want_abs);
   if (!k) return 0;
   size_t smem = smem_bytes(m, n);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
   return nb;
@@ -166,7 +166,7 @@ cudaError_t launch_ryser_f64(const SweepArgs& a, const SizeWeights& weights, con
   void* k = pick(a.m, weighted, want_abs);
   if (!k) return cudaErrorInvalidValue;
   size_t smem = smem_bytes(a.m, a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

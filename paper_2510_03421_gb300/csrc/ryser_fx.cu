@@ -252,7 +252,7 @@ int ryser_fx_blocks_per_sm(int m, int n, int block, bool want_abs) {
   void* k = pick(m, want_abs);
   if (!k) return 0;
   const size_t smem = smem_bytes(m, n);
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (smem > 32 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
@@ -267,7 +267,7 @@ cudaError_t launch_ryser_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = smem_bytes(a.m, a.n);
-  if (smem > 48 * 1024) {
+  if (smem > 32 * 1024) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

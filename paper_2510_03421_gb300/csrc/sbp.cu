@@ -336,7 +336,7 @@ int sbp_run(perm_handle_s* h, const double* dC, int64_t ld, int n, int N, int dt
   void* k = integer ? pick_fx(n) : (W == 2 ? pick_w<2>(n) : pick_w<1>(n));
   if (!k) return 1;
   const size_t smem = integer ? (size_t)n * N * sizeof(long long) : (size_t)W * n * N * sizeof(double);
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (smem > 32 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                               cudaSuccess)
     return 2;
   int bps = 0;

@@ -72,7 +72,7 @@ def scale(A, kind="glynn"):
     if m == 0:
         s = 1.0
     elif kind == "glynn":
-        if A.dtype.kind == "f" and m < n:
+        if m < n:
             # the grouped evaluation of the same sum of |term| (cheap for small m)
             s = oracle.glynn_rect_grouped_abs(A, prec="f64") / (2.0 ** (n - 1) * math.factorial(n - m))
         else:
@@ -115,8 +115,11 @@ def auto_scale(capi, A, dev, exhaustive=False):
     A = np.asarray(A)
     cplx = A.dtype.kind == "c"
     kinds = {capi.PERM_CAND_COMBINATORIC: ("definition", U), capi.PERM_CAND_RYSER: ("ryser", U),
-             capi.PERM_CAND_GLYNN: (default_kind(A, 0), U_CFIX if cplx else U),
-             capi.PERM_CAND_GLYNN_FIXED: (default_kind(A, 2), U_CFIX if cplx else U)}
+             capi.PERM_CAND_GLYNN: (default_kind(A, 0) if cplx else "glynn", U_CFIX if cplx else U),
+             capi.PERM_CAND_GLYNN_FIXED: (default_kind(A, 3), U),
+             capi.PERM_CAND_RYSER_FP64: ("ryser", U), capi.PERM_CAND_GLYNN_DMMA: ("glynn", U),
+             capi.PERM_CAND_GLYNN_INT: (default_kind(A, 2), U),
+             capi.PERM_CAND_GLYNN_SHORT: ("glynn" if cplx else default_kind(A, 3), U)}
     if exhaustive:
         return max(scale(A, k) for k, _ in kinds.values()), max(u for _, u in kinds.values())
     cand, _ = capi.perm_auto_choice(to_dev(A, dev))

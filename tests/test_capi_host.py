@@ -91,7 +91,7 @@ def test_damaged_cost_model_file_is_refused(tmp_path):
 
     from paper_2510_03421_gb300 import costmodel
     w, dims, meta = costmodel.load()  # the shipped model loads
-    assert dims[0] == 12 and dims[2] == 4 and np.all(np.isfinite(w))
+    assert dims[0] == 12 and dims[2] == 8 and np.all(np.isfinite(w))
     bad = tmp_path / "bad.npz"
     bad.write_bytes(b"not an npz archive")
     with pytest.raises(ValueError):

@@ -96,6 +96,25 @@ def test_haar_blocks_split_items_and_host_buffers(capi, dev):
         assert capi.value(host_out, capi.PERM_C128, b) == got[b]
 
 
+_truths = {}
+
+
+def _truth(key, A):
+    """Long-double truth, computed once per matrix across the parametrised runs: Glynn
+    for squares and near-squares, the by-combination rectangular Ryser otherwise (a
+    padded Glynn sum over 2^(n-1) terms in software quad precision takes minutes)."""
+    if key not in _truths:
+        m, n = sorted(A.shape)
+        B = A if A.shape[0] <= A.shape[1] else A.T
+        if m == n:
+            _truths[key] = oracle.glynn(A)
+        elif A.dtype.kind == "f":
+            _truths[key] = oracle.glynn_rect_grouped(B)
+        else:
+            _truths[key] = oracle.ryser_rect(B)
+    return _truths[key]
+
+
 @pytest.mark.parametrize("arith", [0, 1, 2, 3])
 def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     # padded orders 16..32 (n = 13..32) are warp items; by default they run on the integer
@@ -103,8 +122,8 @@ def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     # a share of each product on the FP64 unit, with FIXED without it.  Square,
     # rectangular and transposed shapes, a matrix with a non-finite entry, an empty one.
     import torch
-    g = inputs.rng(9650 + arith)
-    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (21, 23), (6, 26), (22, 22), (0, 18),
+    g = inputs.rng(9650)
+    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (18, 21), (6, 26), (20, 20), (0, 18),
               (12, 18)]
     mats = [(g.standard_normal(s) + 1j * g.standard_normal(s)) / np.sqrt(2 * max(s)) for s in shapes]
     mats[-1][3, 4] = np.nan
@@ -113,15 +132,14 @@ def test_complex_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     out = capi.perm_batched(tp, to, tM, tN, opts=dict(arith=arith))
     torch.cuda.synchronize(dev)
     got = results(capi, out, capi.PERM_C128, len(mats))
-    live = [k for k, A in enumerate(mats[:-1]) if min(A.shape) > 0]
-    truth = dict(zip(live, oracle_many("glynn", [mats[k] for k in live])))
     for k, (A, x) in enumerate(zip(mats[:-1], got[:-1])):
         if min(A.shape) == 0:
             assert x == 1
             continue
-        close(x, truth[k], A, u=U_CFIX)
+        ref = _truth(("c", k), A)
+        close(x, ref, A, u=U_CFIX)
         if A.shape[0] == A.shape[1]:
-            assert tol_ratio(truth[k], A, u=U_CFIX) <= 1e-9
+            assert tol_ratio(ref, A, u=U_CFIX) <= 1e-9
     assert np.isnan(got[-1].real) and np.isnan(got[-1].imag)
 
 
@@ -131,8 +149,8 @@ def test_real_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     # default, on the FP64 class kernels with opts.arith = FP64; MIXED forces the FP64
     # share of each product, FIXED forbids it
     import torch
-    g = inputs.rng(9670 + arith)
-    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (21, 23), (6, 26), (23, 23), (0, 18),
+    g = inputs.rng(9670)
+    shapes = [(13, 13), (14, 16), (16, 16), (17, 20), (20, 17), (19, 19), (21, 23), (6, 26), (22, 22), (0, 18),
               (6, 30), (12, 18)]
     mats = [g.uniform(-1, 1, s) for s in shapes]
     mats[-1][3, 4] = np.inf
@@ -141,13 +159,12 @@ def test_real_warp_classes_integer_pipes_and_fp64(capi, dev, arith):
     out = capi.perm_batched(tp, to, tM, tN, opts=dict(arith=arith))
     torch.cuda.synchronize(dev)
     got = results(capi, out, capi.PERM_F64, len(mats))
-    for A, x in zip(mats[:-1], got[:-1]):
+    for k, (A, x) in enumerate(zip(mats[:-1], got[:-1])):
         m, n = sorted(A.shape)
         if m == 0:
             assert x == 1.0
             continue
-        B = A if A.shape[0] <= A.shape[1] else A.T
-        ref = oracle.glynn(A) if n <= 23 and m == n or n <= 20 else oracle.glynn_rect_grouped(B)
+        ref = _truth(("r", k), A)
         close(x, ref, A)
         if m == n:
             assert tol_ratio(ref, A) <= 1e-9

@@ -142,7 +142,9 @@ def test_mixed_is_default_and_error_bound_holds(capi, dev):
     torch.cuda.synchronize(dev)
     got = capi.value(out, capi.PERM_F64)
     assert abs(got - ref) <= float(err.item()) + 2 * U * abs(ref)
-    assert got == run(capi, "perm_glynn", A, dev, MIXED)
+    # without a bound the default is the mixed sweep (the bound variant differs in the
+    # last bits: it takes exact magnitudes of the column sums)
+    assert run(capi, "perm_glynn", A, dev) == run(capi, "perm_glynn", A, dev, MIXED)
 
 
 def test_mixed_sampled_n36_against_oracle_partials(capi, dev):

@@ -584,6 +584,7 @@ def test_glynn_abs_all_ones_rectangle(m, n):
     exact = float(_glynn_ones_abs(n))
     A = np.ones((m, n))
     assert _rel(oracle.glynn_rect_grouped_abs(A), exact) < 1e-15
+    assert _rel(oracle.glynn_rect_grouped_abs(A.astype(complex)), exact) < 1e-15
     if n <= 14:
         assert _rel(oracle.glynn_partial_abs(A, 0, 1 << (n - 1)), exact) < 1e-15
         assert _rel(oracle.glynn_partial_abs(A.astype(complex), 0, 1 << (n - 1)), exact) < 1e-15
@@ -712,3 +713,10 @@ def test_ryser_abs_by_size_equals_gray_enumeration(m, n):
     A = inputs.rng(740 + m + n).uniform(-1, 1, (m, n))
     assert _rel(oracle.ryser_abs(A), oracle.ryser_partial_abs(A, 0, 1 << n)) < 1e-14
     assert _rel(oracle.ryser_abs(np.ones((m, n))), _ryser_ones_abs(m, n)) < 1e-15
+
+
+@pytest.mark.parametrize("m,n", [(2, 6), (4, 9), (6, 11)])
+def test_complex_grouped_abs_equals_ungrouped(m, n):
+    g = inputs.rng(760 + m + n)
+    A = g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))
+    assert _rel(oracle.glynn_rect_grouped_abs(A), oracle.glynn_partial_abs(A, 0, 1 << (n - 1))) < 1e-14
