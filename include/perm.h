@@ -135,7 +135,12 @@ int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_
  * product of the blocks' permanents, and a dense real square matrix of order >= 24
  * whose entries are 1/(x_i - y_j) within 2^-48 relative, all of one sign, is evaluated
  * by Borchardt's theorem on the fitted points (perm_cauchy), the error bound widened
- * by n 2^-48 (1 + n 2^-48) |per| for the fit. */
+ * by n 2^-48 (1 + n 2^-48) |per| for the fit.
+ * Cost of that structure pass: the matrix is copied to the host and `stream` is
+ * synchronised before the sweep is launched (at most 64 KiB of copy, microseconds;
+ * but the call does not return before the stream's earlier work has finished, so it
+ * cannot be captured in a CUDA graph).  Ryser candidates take real input only; the
+ * FP64 configurations among the candidates are offered for square matrices only. */
 int perm_auto(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
               void* stream, const perm_opts* opts);
 

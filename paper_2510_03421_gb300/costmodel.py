@@ -11,8 +11,8 @@ argmin.  This module:
 
 * times candidates on a seeded grid of (m, n, density, dtype) cells
   (``measure_grid``), extrapolating sweeps too long to run from a timed term range;
-* trains the model with ``capi.perm_mlp_train`` and installs it with
-  ``capi.perm_set_cost_model``;
+* trains the model with ``capi.perm_mlp_train`` on each cell's regret (log2 time over
+  the cell's fastest candidate) and installs it with ``capi.perm_set_cost_model``;
 * refits the paper's rule (``PaperRule``) on the same timings as a baseline;
 * scores policies on a held-out batch against exhaustive timing (``evaluate``).
 
@@ -182,13 +182,17 @@ def time_candidate(timer, dA, m, n, density, code, cand, reps=3):
     return part * 2.0 ** (lw - work_log2(mm, nn, density, cand))
 
 
-def grid_cells(count, seed):
-    """A seeded sample of the (m, n, density, dtype) grid: m in 2..40, n in m..60."""
+def grid_cells(count, seed, small_frac=0.5, small_n=26):
+    """A seeded sample of the (m, n, density, dtype) grid: m in 2..40, n in m..60; a
+    fraction `small_frac` drawn from n <= small_n, where the candidates' times are
+    close, every candidate is timed in full and most matrices of a mixed batch are."""
     g = inputs.rng(seed)
     cells = []
     pairs = [(m, n) for m in range(2, 41) for n in range(m, 61)]
-    for _ in range(count):
-        m, n = pairs[int(g.integers(len(pairs)))]
+    small = [(m, n) for (m, n) in pairs if n <= small_n]
+    for k in range(count):
+        pool = small if k < small_frac * count else pairs
+        m, n = pool[int(g.integers(len(pool)))]
         d = float(g.choice([0.1, 0.5, 1.0]))
         dt = str(g.choice(list(DTYPES)))
         cells.append((m, n, d, dt))
@@ -237,6 +241,18 @@ def fill_combinatoric(X, T, Mk, rows):
             T[i, 0] = work_log2(m, n, d, 0) + float(np.median(offs[dt]))
             Mk[i, 0] = 1.0
     return T, Mk
+
+
+def regret(T, Mk):
+    """Targets relative to each cell's fastest candidate (log2 time - log2 best): the
+    choice depends only on these differences, and the absolute scale (2^-15 .. 2^10 s
+    across the grid) would otherwise take the model's capacity."""
+    T = T.copy()
+    for i in range(len(T)):
+        live = Mk[i] > 0
+        if live.any():
+            T[i, live] -= T[i, live].min()
+    return T
 
 
 def train(dev, X, T, Mk, epochs=600, batch=128, lr=3e-3, seed=7):
@@ -411,7 +427,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--cells", type=int, default=3000)
     ap.add_argument("--eval", type=int, default=10000)
-    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--epochs", type=int, default=1500)
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--report", default=None)
     a = ap.parse_args()
@@ -423,7 +439,7 @@ def main():
     X, T, Mk, rows = measure_grid(dev, cells, seed0=inputs.SEED_BASE * 10, log=log)
     T, Mk = fill_combinatoric(X, T, Mk, rows)
     t1 = time.time()
-    w, hist = train(dev, X, T, Mk, epochs=a.epochs)
+    w, hist = train(dev, X, regret(T, Mk), Mk, epochs=a.epochs)
     t2 = time.time()
     rule = PaperRule().fit(rows, T, Mk)
     res = evaluate(dev, w, rule, a.eval, inputs.SEED_BASE + 6, log=log)

@@ -16,9 +16,10 @@
 // only on the set of free columns.  For n <= 16 (not for Gaussian integers) the block
 // first tabulates, for every column triple a < b < c, the sum of the six products
 // a_{r0 x} a_{r1 y} a_{r2 z} over the orderings (x, y, z) of (a, b, c) -- the same
-// leaf products the search would form -- and the search stops three rows early,
-// adding the table entries of the triples of free columns.  That removes the three
-// deepest levels of the tree, which hold all but a sixth of its nodes.
+// leaf products the search would form -- and the search stops four rows early: for
+// each nonzero free column x of the fourth-last row it adds a_x times the table entries
+// of the triples of the remaining free columns.  That removes the four deepest levels
+// of the tree from the search, which hold all but a 24th of its nodes.
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -176,28 +177,44 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
       int k = depth;
       cand[k] = rowmask[k] & ~used;
       val[k] = F::zero();
+      // sum of the table entries over the triples of the column set fm
+      auto triples = [&](unsigned long long fm) {
+        T s = F::zero();
+        unsigned long long xm = fm;
+        while (xm) {
+          const int x = __ffsll((long long)xm) - 1;
+          xm &= xm - 1;
+          unsigned long long ym = xm;
+          while (ym) {
+            const int y = __ffsll((long long)ym) - 1;
+            ym &= ym - 1;
+            unsigned long long zm = ym;
+            while (zm) {
+              const int z = __ffsll((long long)zm) - 1;
+              zm &= zm - 1;
+              s = F::add(s, sT[(x * n + y) * n + z]);
+            }
+          }
+        }
+        return s;
+      };
       while (true) {
-        if (tail && k == m - 3) {
-          // three rows left: the triples of free columns, from the table
-          T s = F::zero();
+        if (tail && k == m - 4) {
+          // four rows left: each nonzero free column x of row k times the table sum
+          // over the rest, without descending
           const unsigned long long fm = allcols & ~used;
-          unsigned long long xm = fm;
+          unsigned long long xm = rowmask[k] & fm;
+          T s = F::zero();
           while (xm) {
             const int x = __ffsll((long long)xm) - 1;
             xm &= xm - 1;
-            unsigned long long ym = xm;
-            while (ym) {
-              const int y = __ffsll((long long)ym) - 1;
-              ym &= ym - 1;
-              unsigned long long zm = ym;
-              while (zm) {
-                const int z = __ffsll((long long)zm) - 1;
-                zm &= zm - 1;
-                s = F::add(s, sT[(x * n + y) * n + z]);
-              }
-            }
+            s = F::fma(sA[k * n + x], triples(fm & ~(1ull << x)), s);
           }
           val[k] = s;
+          cand[k] = 0;
+        } else if (tail && k == m - 3) {
+          // three rows left: the triples of free columns, from the table
+          val[k] = triples(allcols & ~used);
           cand[k] = 0;
         } else if (k == m - 1) {
           T s = F::zero();

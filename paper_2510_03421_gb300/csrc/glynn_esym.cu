@@ -178,7 +178,11 @@ __global__ void __launch_bounds__(kEsymBlock) glynn_esym_kernel(SweepArgs a, con
       e_lo += p - kMaxLsb;
       p = kMaxLsb;
     }
-    acc_add(x0, x1, x2, P, p, vneg);
+    if (p >= 0) {
+      acc_add_nb(x0, x1, x2, P, p, vneg);
+    } else {
+      acc_add(x0, x1, x2, P, p, vneg);
+    }
   };
 
   for (uint64_t r = warp; r < rounds; r += warps) {

@@ -90,7 +90,7 @@ __global__ void fx_prep_kernel(SweepArgs a, FxTable* tab) {
 
 template <int N, int K, bool ABS>
 __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
-  extern __shared__ long long smem_fx[];
+  extern __shared__ __align__(16) long long smem_fx[];
   __shared__ dd scratch[3 * 32];
   const int n = a.n;
   long long* sP = smem_fx;          // +2 q_ij
@@ -173,8 +173,14 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(Swee
       } else {
         const int b = ctz64(g);
         const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N;
+        // rows start on 32-byte boundaries (N is a multiple of 4): 16-byte broadcast loads
+        const longlong2* row2 = reinterpret_cast<const longlong2*>(row);
 #pragma unroll
-        for (int j = 0; j < N; ++j) S[j] += row[j];
+        for (int j = 0; j < N / 2; ++j) {
+          const longlong2 v = row2[j];
+          S[2 * j] += v.x;
+          S[2 * j + 1] += v.y;
+        }
       }
       u64 P;
       int E;

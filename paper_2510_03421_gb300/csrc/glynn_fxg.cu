@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fxg_kernel(Sweep
   // m/2 units (the padding rows are exact)
   const bool use_eta = ABS && tab->inexact != 0;
   const long long eta = (a.m + 1) / 2;
-  extern __shared__ long long smem_fx[];
+  extern __shared__ __align__(16) long long smem_fx[];
   __shared__ dd scratch[3 * 32];
   __shared__ u64 s_wm[64];  // C(n - m, t) = s_wm[t] 2^(s_we[t] - 64), s_wm normalised
   __shared__ int s_we[64];
@@ -78,7 +78,11 @@ __global__ void __launch_bounds__(192, (N <= 36) ? 2 : 1) glynn_fxg_kernel(Sweep
       e_lo += p - kMaxLsb;
       p = kMaxLsb;
     }
-    acc_add(x0, x1, x2, P, p, neg);
+    if (p >= 0) {
+      acc_add_nb(x0, x1, x2, P, p, neg);  // no divergence on the sign or the position
+    } else {
+      acc_add(x0, x1, x2, P, p, neg);
+    }
   };
   auto weigh = [&](u64& P, int& E, int t) {
     const u64 h2 = __umul64hi(P, s_wm[t]);

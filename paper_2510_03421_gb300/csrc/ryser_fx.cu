@@ -127,7 +127,11 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) ryser_fx_kernel(Swee
       e_lo += p - kMaxLsb;
       p = kMaxLsb;
     }
-    acc_add(x0, x1, x2, P, p, neg);
+    if (p >= 0) {
+      acc_add_nb(x0, x1, x2, P, p, neg);  // no divergence on the sign or the position
+    } else {
+      acc_add(x0, x1, x2, P, p, neg);
+    }
   };
   // the weight of size s times P 2^E, renormalised
   auto weigh = [&](u64& P, int& E, int s) {
