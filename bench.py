@@ -184,10 +184,11 @@ def run_reference(args):
 # and pipe utilisations, from one ncu capture of this kernel (label says which); the
 # bench times the kernel itself and scales by its own terms/s.
 ISSUE_PROFILE = {
-    36: {"instructions_per_term": 896.0, "dram_bytes_per_launch": 562688,
-         "pipes": {"alu": 0.628, "fp64": 0.614, "fma": 0.276, "issue": 0.573},
-         "label": "ncu capture of glynn_fx_kernel<36, 8, false> at n = 34 (instructions scale per term; "
-                  "DRAM traffic does not grow with the term count)"},
+    36: {"instructions_per_term": 887.7, "dram_bytes_per_launch": 90112,
+         "pipes": {"alu": 0.634, "fp64": 0.618, "fma": 0.272, "issue": 0.571},
+         "label": "ncu --set full capture of glynn_fx_kernel<36, 8, false> at n = 34 (2^33 terms: 2.383e11 warp "
+                  "instructions, 32.0 threads per instruction; instructions scale per term, DRAM traffic does "
+                  "not grow with the term count)"},
 }
 
 
