@@ -28,12 +28,28 @@ def to_integer_matrix(A):
     return Z, s
 
 
-def definition(A) -> Fraction:
+def definition(A):
     """Sum over the injective maps rows -> columns of the products (Eq.
-    rectangular_permanent_definition), exactly; tiny matrices only."""
-    A = np.asarray(A, dtype=np.float64)
+    rectangular_permanent_definition), exactly; tiny matrices only.  Real input gives
+    a Fraction, complex input a pair (re, im) of Fractions."""
+    A = np.asarray(A)
     if A.shape[0] > A.shape[1]:
         A = A.T
+    if A.dtype.kind == "c":
+        m, n = A.shape
+        R, s = to_integer_matrix(np.concatenate([A.real, A.imag], axis=0))
+        re, im = R[:m], R[m:]
+        tr, ti = 0, 0
+        for sigma in permutations(range(n), m):
+            pr, pi = 1, 0
+            for i in range(m):
+                ar, ai = re[i][sigma[i]], im[i][sigma[i]]
+                pr, pi = pr * ar - pi * ai, pr * ai + pi * ar
+            tr += pr
+            ti += pi
+        den = 1 << (s * m)
+        return Fraction(tr, den), Fraction(ti, den)
+    A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     Z, s = to_integer_matrix(A)
     total = 0

@@ -209,23 +209,28 @@ int glynn_dmma(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   const bool want_abs = c.dErr != nullptr;
   const int block = c.o.block ? c.o.block : 256;
   int bps = glynn_dmma_blocks_per_sm(c.n, block, want_abs);
-  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 32, kRealRecord * sizeof(double));
+  LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 32, (want_abs ? kCplxRecord : kRealRecord) * sizeof(double));
   lc.stream = c.stream;
   SweepArgs a = sweep_args(c, g0, g1, 14);
   if (!c.o.chunk_log2) {
-    // chunks of 2^k terms, at least four rounds of 32 chunks per resident warp
+    // chunks of 2^k terms, at least four rounds of 32 chunks per resident warp; with an
+    // error bound at most 2^8 (the drift part of the bound grows with the chunk)
     const uint64_t warps = (uint64_t)lc.grid * (lc.block / 32);
-    int k = 16;
+    int k = want_abs ? 8 : 16;
     while (k > 2 && ((g1 - g0) >> k) < 128 * warps) --k;
     a.chunk_log2 = k;
   }
   if (launch_glynn_dmma(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
+  // as for the FP64 sweep: products and the Kahan sum against sum |term|, the column
+  // sums' errors through the per-term widened products
   const double u = 1.1102230246251565e-16;
-  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
-  const double coef = u * ((double)c.n + 4.0 + 2.0 * (double)c.n * L);
-  if (launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
-                         static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
-    return PERM_ECUDA;
+  const double coef = u * ((double)c.n + 4.0);
+  const cudaError_t f =
+      want_abs ? launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                                     static_cast<double*>(c.dOut), c.dErr, raw, c.stream, 2.0 * u * (c.n + 1))
+               : launch_finish_real(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
+                                    static_cast<double*>(c.dOut), nullptr, raw, c.stream);
+  if (f != cudaSuccess) return PERM_ECUDA;
   return PERM_OK;
 }
 
@@ -466,12 +471,12 @@ int glynn_cplx(Call& c, bool raw, uint64_t g0, uint64_t g1) {
   int bps = glynn_c128_blocks_per_sm(c.n, c.o.block ? c.o.block : block, want_abs);
   LaunchCfg lc = plan_grid(c.h, c.o, block, bps, g1 - g0, 16, kCplxRecord * sizeof(double));
   lc.stream = c.stream;
-  SweepArgs a = sweep_args(c, g0, g1, 14);
+  SweepArgs a = sweep_args(c, g0, g1, want_abs ? 8 : 14);  // shorter chunks bound the drift tighter
   if (launch_glynn_c128(a, lc, want_abs) != cudaSuccess) return PERM_ECUDA;
-  const double u = 1.1102230246251565e-16;
-  const double L = (double)(1ull << (a.chunk_log2 < 62 ? a.chunk_log2 : 62));
-  // complex products: each rounds by at most about 2 sqrt(2) u
-  const double coef = u * (3.0 * (double)c.n + 6.0 + 2.0 * (double)c.n * L);
+  // the bound variant accumulates each term's full bound (rounding of the products and
+  // the widened difference for the column sums' errors); its own FP64 sum of positive
+  // terms is inflated by 2^-20
+  const double coef = 1.0 + 0x1p-20;
   if (launch_finish_cplx(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m, coef,
                          static_cast<double*>(c.dOut), c.dErr, raw, c.stream) != cudaSuccess)
     return PERM_ECUDA;

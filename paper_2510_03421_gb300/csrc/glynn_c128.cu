@@ -36,6 +36,7 @@ template <int N, bool ABS>
 __global__ void __launch_bounds__(128) glynn_c128_kernel(SweepArgs a) {
   extern __shared__ double smem[];
   __shared__ dd scratch[3 * 32];
+  __shared__ double s_eps[ABS ? N : 1];
   const int n = a.n, m = a.m;
   // interleaved (re, im) pairs: +2 a'_ij then -2 a'_ij
   double2* sP = reinterpret_cast<double2*>(smem);
@@ -51,6 +52,24 @@ __global__ void __launch_bounds__(128) glynn_c128_kernel(SweepArgs a) {
     sP[idx] = make_double2(2.0 * v.x, 2.0 * v.y);
     sM[idx] = make_double2(-2.0 * v.x, -2.0 * v.y);
   }
+  if (ABS) {
+    // modulus of a column sum's error: the rebuild ((n - 1) u) and the at most
+    // 2^chunk_log2 - 1 later updates (u each), per component, against
+    // sum_i |re a'_ij| + |im a'_ij| (first order)
+    const double steps = (double)n + ldexp(1.0, a.chunk_log2 < 62 ? a.chunk_log2 : 62);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double colabs = 0.0;
+      if (j < n)
+        for (int i = 0; i < n; ++i) {
+          const int64_t e = 2 * (i * a.rs + j * a.cs);
+          colabs += (i < m) ? fabs(A[e]) + fabs(A[e + 1]) : 1.0;
+        }
+      s_eps[j] = steps * 0x1p-53 * colabs * (1.0 + 0x1p-40);
+    }
+  }
+  // per term of the bound variant: the products' rounding (3n + 6) u and the FP64
+  // evaluation of the widened product 2 (n + 1) u, against |re t| + |im t|
+  const double cr = ldexp(3.0 * n + 6.0 + 2.0 * (n + 1.0), -53);
   __syncthreads();
 
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -101,7 +120,21 @@ __global__ void __launch_bounds__(128) glynn_c128_kernel(SweepArgs a) {
     sum = __dadd_rn(acci, y);
     compi = __dsub_rn(__dsub_rn(sum, acci), y);
     acci = sum;
-    if (ABS) absacc = __dadd_rn(absacc, __dadd_rn(fabs(t.re), fabs(t.im)));
+    if (ABS) {
+      // bound of this term's error: cr |t|_1 plus prod (|S_j|_1 + eps_j) - prod |S_j|_1,
+      // which bounds the effect of the column sums' errors (|.|_1 >= the modulus, and
+      // the widened difference grows with the sums it is formed from)
+      const double t1 = __dadd_rn(fabs(t.re), fabs(t.im));
+      double pe = 1.0, pa = 1.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const double sa = __dadd_rn(fabs(Sr[j]), fabs(Si[j]));
+        pe = __dmul_rn(pe, __dadd_rn(sa, s_eps[j]));
+        pa = __dmul_rn(pa, sa);
+      }
+      const double d = fmax(__dsub_rn(pe, pa), 0.0);
+      absacc = __dadd_rn(absacc, __fma_rn(cr, fmax(t1, pa) + d, d * (1.0 + 0x1p-25)));
+    }
   }
 
   dd v[3] = {two_sum(accr, -compr), two_sum(acci, -compi), dd{absacc, 0.0}};

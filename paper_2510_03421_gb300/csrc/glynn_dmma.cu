@@ -30,7 +30,8 @@ template <int N, bool ABS>
 __global__ void __launch_bounds__(256) glynn_dmma_kernel(SweepArgs a) {
   constexpr int NT = (N + 7) / 8;  // column tiles
   extern __shared__ double smem[];
-  __shared__ dd scratch[2 * 32];
+  __shared__ dd scratch[3 * 32];
+  __shared__ double s_eps[ABS ? N : 1];
   const int n = a.n, m = a.m;
   double* sP = smem;          // +2 a'_ij
   double* sM = smem + n * N;  // -2 a'_ij
@@ -42,6 +43,18 @@ __global__ void __launch_bounds__(256) glynn_dmma_kernel(SweepArgs a) {
     sP[idx] = 2.0 * v;
     sM[idx] = -2.0 * v;
   }
+  if (ABS) {
+    // a contracted column sum errs by at most (n - 1) u sum_i |a'_ij| (n exact +-a
+    // products summed), each of the at most 2^chunk_log2 - 1 later updates by
+    // u sum_i |a'_ij| (first order), as in glynn_f64.cu
+    const double steps = (double)n + ldexp(1.0, a.chunk_log2 < 62 ? a.chunk_log2 : 62);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      double colabs = 0.0;
+      if (j < n)
+        for (int i = 0; i < n; ++i) colabs += fabs((i < m) ? A[i * a.rs + j * a.cs] : 1.0);
+      s_eps[j] = steps * 0x1p-53 * colabs * (1.0 + 0x1p-40);
+    }
+  }
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -52,7 +65,7 @@ __global__ void __launch_bounds__(256) glynn_dmma_kernel(SweepArgs a) {
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
 
-  double acc = 0.0, comp = 0.0, absacc = 0.0;
+  double acc = 0.0, comp = 0.0, absacc = 0.0, diffacc = 0.0;
   double S[N];
   for (uint64_t r = warp; r < rounds; r += warps) {
     const uint64_t chunk = c_first + 32 * r + lane;
@@ -110,18 +123,29 @@ __global__ void __launch_bounds__(256) glynn_dmma_kernel(SweepArgs a) {
       const double sum = __dadd_rn(acc, y);
       comp = __dsub_rn(__dsub_rn(sum, acc), y);
       acc = sum;
-      if (ABS) absacc = __dadd_rn(absacc, fabs(t));
+      if (ABS) {
+        absacc = __dadd_rn(absacc, fabs(t));
+        double pe = 1.0;  // prod (|S_j| + eps_j): the column sums' own errors
+#pragma unroll
+        for (int j = 0; j < N; ++j) pe = __dmul_rn(pe, __dadd_rn(fabs(S[j]), s_eps[j]));
+        diffacc = __dadd_rn(diffacc, __dsub_rn(pe, fabs(t)));
+      }
     }
   }
 
-  dd v[2] = {two_sum(acc, -comp), dd{absacc, 0.0}};
-  block_sum_dd<2>(v, scratch);
+  // records {sum, sum |term|, sum of the widened differences} (the last two with ABS)
+  dd v[3] = {two_sum(acc, -comp), dd{absacc, 0.0}, dd{diffacc, 0.0}};
+  block_sum_dd<3>(v, scratch);
   if (threadIdx.x == 0) {
-    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * (ABS ? kCplxRecord : kRealRecord);
     rec[0] = v[0].hi;
     rec[1] = v[0].lo;
     rec[2] = v[1].hi;
     rec[3] = v[1].lo;
+    if (ABS) {
+      rec[4] = v[2].hi;
+      rec[5] = v[2].lo;
+    }
   }
 }
 

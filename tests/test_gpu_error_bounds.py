@@ -14,7 +14,8 @@ from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-GLYNN_ARITH = {"auto": 0, "fp64": 1, "fixed": 2, "mixed": 3}
+GLYNN_ARITH = {"auto": dict(arith=0), "fp64": dict(arith=1), "fixed": dict(arith=2), "mixed": dict(arith=3),
+               "fp64_tensor_core_start": dict(arith=1, start=2)}
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +80,7 @@ CASES = [("cancel 12", lambda: cancelling(12, 501)), ("cancel 18", lambda: cance
 def test_glynn_bound_holds(capi, dev, arith, name, make):
     A = make()
     ref = truth(name, A)
-    got, err = bounded(capi, dev, "perm_glynn", A, dict(arith=GLYNN_ARITH[arith]))
+    got, err = bounded(capi, dev, "perm_glynn", A, GLYNN_ARITH[arith])
     assert err >= 0.0, "no bound stated"
     assert abs(got - ref) <= err, (name, arith, got, ref, abs(got - ref), err)
 
@@ -103,3 +104,36 @@ def test_bound_is_tight_on_well_conditioned_input(capi, dev):
     for arith, limit in ((0, 1e-10), (1, 1e-9), (2, 1e-10), (3, 1e-10)):
         got, err = bounded(capi, dev, "perm_glynn", A, dict(arith=arith))
         assert abs(got - ref) <= err <= limit * abs(ref), (arith, err / abs(ref))
+
+
+def complex_cancelling(n, seed):
+    g = inputs.rng(seed)
+    A = g.uniform(-1, 1, (n, n)) + 1j * g.uniform(-1, 1, (n, n))
+    A[:, 1] = 1.0 + 1.0j
+    A[n - 1, 1] = -(n - 1.0) * (1.0 + 1.0j)
+    A[:, 1] += 1e-12 * (g.uniform(-1, 1, n) + 1j * g.uniform(-1, 1, n))
+    return A
+
+
+def complex_wide(n, seed):
+    g = inputs.rng(seed)
+    return (g.uniform(-1, 1, (n, n)) + 1j * g.uniform(-1, 1, (n, n))) * np.exp2(g.integers(-30, 31, (n, n)))
+
+
+@pytest.mark.parametrize("name,make", [("cancel c8", lambda: complex_cancelling(8, 511)),
+                                       ("wide c7", lambda: complex_wide(7, 512)),
+                                       ("identity c6x9", lambda: padded_identity(6, 9) + 0j)],
+                         ids=["cancel c8", "wide c7", "identity c6x9"])
+def test_complex_glynn_bound_holds(capi, dev, name, make):
+    # a complex call that asks for a bound takes the FP64 sweep; the bound covers the
+    # modulus of the error
+    import torch
+    A = make()
+    re, im = exact.definition(A)
+    ref = complex(float(re), float(im))
+    err = torch.full((1,), -2.0, dtype=torch.float64, device=dev)
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(err=err))
+    torch.cuda.synchronize(dev)
+    got = capi.value(out, capi.PERM_C128)
+    e = float(err.item())
+    assert e >= 0.0 and abs(got - ref) <= e, (name, got, ref, abs(got - ref), e)

@@ -720,3 +720,18 @@ def test_complex_grouped_abs_equals_ungrouped(m, n):
     g = inputs.rng(760 + m + n)
     A = g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))
     assert _rel(oracle.glynn_rect_grouped_abs(A), oracle.glynn_partial_abs(A, 0, 1 << (n - 1))) < 1e-14
+
+
+def test_exact_complex_definition():
+    from oracle import exact
+    g = inputs.rng(820)
+    A = g.uniform(-1, 1, (4, 5)) + 1j * g.uniform(-1, 1, (4, 5))
+    re, im = exact.definition(A)
+    ref = oracle.definition(A)
+    assert _rel(complex(float(re), float(im)), ref) < 1e-15
+    B = A.real.copy()
+    re, im = exact.definition(B + 0j)
+    assert im == 0 and re == exact.definition(B)
+    # per(i I) = i^n
+    re, im = exact.definition(1j * np.eye(3))
+    assert (re, im) == (0, -1)
