@@ -90,7 +90,10 @@ typedef enum {
 
 typedef struct {
   int32_t chunk_log2;   /* terms between exact re-anchoring of the column sums (0 = planner) */
-  int32_t block;        /* threads per block (0 = planner) */
+  int32_t block;        /* threads per block (0 = planner).  The real square sweep on the
+                           integer pipes from n = 37 (mixed arithmetic, no error bound)
+                           runs a lane pair per term in 256-thread blocks; a block of at
+                           most 128 threads selects the one-lane kernel there */
   int32_t grid;         /* blocks (0 = planner: a multiple of the SM count) */
   int32_t arith;        /* perm_arith */
   int32_t start;        /* perm_start */

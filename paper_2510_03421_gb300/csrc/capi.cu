@@ -287,15 +287,19 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
   if (!raw && use_esym(c)) return glynn_esym_run(c);
   // a whole rectangular permanent: the grouped walk over the real rows' sign vectors
   const bool grouped = !raw && c.m < c.n;
-  // 6 warps, two blocks per SM at up to 168 registers (square kernel from N = 40: 4 warps)
-  const int block = grouped ? 192 : glynn_fx_block(c.n);
-  if (c.o.block > block) return PERM_EINVAL;
+  // the lane-pair sweep (24 warps per SM) for a mixed square sweep without a bound,
+  // unless a block of at most the one-lane kernel's size is asked for; otherwise 6
+  // warps, two blocks per SM at up to 168 registers (from N = 40: 4 warps)
+  const bool pair = !grouped && mixed && !want_abs && glynn_fx_pair_available(c.n) &&
+                    (c.o.block == 0 || c.o.block > glynn_fx_block(c.n));
+  const int block = grouped ? 192 : pair ? glynn_fx_pair_block() : glynn_fx_block(c.n);
+  if (c.o.block > block || (pair && c.o.block && c.o.block != block)) return PERM_EINVAL;
   if (grouped) {
     g0 = 0;
     g1 = 1ull << (c.m - 1);
   }
   const int bps = grouped ? glynn_fxg_blocks_per_sm(c.m, c.n, c.o.block ? c.o.block : block)
-                          : glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, mixed);
+                          : glynn_fx_blocks_per_sm(c.n, c.o.block ? c.o.block : block, mixed, pair);
   const uint64_t work = grouped ? (g1 - g0) * (uint64_t)(c.n - c.m + 1) : g1 - g0;
   // with an error bound both sweeps write {sum, sum |term|, eta-widened sum}
   const bool three = want_abs;
@@ -313,14 +317,14 @@ int glynn_fixed(Call& c, bool raw, uint64_t g0, uint64_t g1, bool mixed) {
   // the 192-bit accumulator holds 2^40 maximal terms per chunk (2^6 per grouped step)
   if (a.chunk_log2 > (grouped ? 34 : 40)) return PERM_ETOOBIG;
   const cudaError_t e = grouped ? launch_glynn_fxg(a, fx_table(c.h), lc, want_abs)
-                                : launch_glynn_fx(a, fx_table(c.h), lc, want_abs, mixed);
+                                : launch_glynn_fx(a, fx_table(c.h), lc, want_abs, mixed, pair);
   if (e != cudaSuccess) return PERM_ECUDA;
   // relative error of a term against |term|: n/2 pair products of < 2^-59 each (the
   // running mantissa keeps >= 60 bits), the binomial weight of a grouped term (< 2^-62);
   // the mixed variant's K columns: K conversions and K - 1 multiplications in FP64.
   // The bound variants take exact magnitudes and bound the rounding of A to fixed
   // point by their eta-widened products (zero when every entry was exact)
-  const int K = (mixed && !grouped) ? glynn_fx_mixed_columns(c.n) : 0;
+  const int K = (mixed && !grouped) ? (pair ? glynn_fx_pair_mixed_columns(c.n) : glynn_fx_mixed_columns(c.n)) : 0;
   const double coef = std::ldexp((double)(c.n - K) + 5.0, -60) + std::ldexp(2.0 * K, -53);
   const cudaError_t f = three ? launch_finish_bound(static_cast<const double*>(a.partials), lc.grid, c.n - 1, c.n - c.m,
                                                     coef, static_cast<double*>(c.dOut), c.dErr, raw, c.stream)
@@ -564,6 +568,9 @@ int ryser_fixed(Call& c) {
   }
   // 2^40 maximal terms per 192-bit accumulator
   if (a.chunk_log2 > 40) return PERM_ETOOBIG;
+  // rectangles: chunks in the size-coherent order when there are enough of them
+  // (start_mode 1; a square needs every subset, so order buys it nothing)
+  a.start_mode = (c.m < c.n && c.n - a.chunk_log2 >= 6) ? 1 : 0;
   if (launch_ryser_fx(a, fx_table(c.h), lc, want_abs) != cudaSuccess) return PERM_ECUDA;
   // per term: m/2 pair products (< 2^-59 each), the binomial weight (< 2^-62), and the
   // accumulation; the rounding of A to fixed point is bounded by the eta-widened sum

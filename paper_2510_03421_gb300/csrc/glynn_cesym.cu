@@ -164,8 +164,10 @@ __global__ void __launch_bounds__(kBlock) glynn_cesym_kernel(SweepArgs a, const 
       for (int s = 1; s <= M; ++s) E[s] = csf{0, 0, kZeroExp};
       for (int j = 0; j < n; ++j) {
         const csf c = csf_from_int(myC[2 * j * nt], myC[2 * j * nt + nt], s_e[j]);
+        const int lo = M - (n - 1 - j), hi = j + 1;  // the band that can still reach e_m
 #pragma unroll
-        for (int s = M; s >= 1; --s) E[s] = csf_add(E[s], csf_mul(c, E[s - 1]));
+        for (int s = M; s >= 1; --s)
+          if (s >= lo && s <= hi) E[s] = csf_add(E[s], csf_mul(c, E[s - 1]));
       }
       const csf v = E[M];
       if ((v.re | v.im) != 0) {

@@ -19,7 +19,10 @@
 //   * c_j in fixed point as in glynn_fx.cu, column j scaled by 2^e_j so that
 //     sum_i |a_ij| 2^e_j < 2^60 (real rows only), the Gray-code flips exact int64
 //     additions of +-2 q_ij, held per thread in shared memory;
-//   * e_0..e_m by the recurrence E_s += c_j E_{s-1} (s descending) over the columns, in
+//   * e_0..e_m by the recurrence E_s += c_j E_{s-1} (s descending) over the columns, only
+//     for the s that are reachable (s <= j + 1) and can still reach m (s >= m - (n-1-j)):
+//     m (n - m + 1) multiply-adds per sign vector instead of m n; the band depends on the
+//     loop indices only, so the warp stays converged.  The recurrence runs in
 //     a software float with a signed 64-bit mantissa of magnitude [2^62, 2^63] and an
 //     int exponent: product = high half of the 128-bit product (truncation < 2^-60),
 //     sum = both halves aligned and added (< 2^-61 each), renormalised with clz;
@@ -218,8 +221,10 @@ __global__ void __launch_bounds__(kEsymBlock) glynn_esym_kernel(SweepArgs a, con
       for (int s = 1; s <= M; ++s) E[s] = sf{0, kZeroExp};
       for (int j = 0; j < n; ++j) {
         const sf c = sf_from_int(myC[j * nt], s_e[j]);
+        const int lo = M - (n - 1 - j), hi = j + 1;  // the band that can still reach e_m
 #pragma unroll
-        for (int s = M; s >= 1; --s) E[s] = sf_add(E[s], sf_mul(c, E[s - 1]));
+        for (int s = M; s >= 1; --s)
+          if (s >= lo && s <= hi) E[s] = sf_add(E[s], sf_mul(c, E[s - 1]));
       }
       accumulate(a0, a1, a2, E[M], (unsigned)(g & 1u));
       if (ABS) {
@@ -231,14 +236,17 @@ __global__ void __launch_bounds__(kEsymBlock) glynn_esym_kernel(SweepArgs a, con
         for (int j = 0; j < n; ++j) {
           const long long q = myC[j * nt];
           const sf c = sf_from_int(q < 0 ? -q : q, s_e[j]);
+          const int lo = M - (n - 1 - j), hi = j + 1;
           if (use_f) {
             const sf ce = sf_from_int((q < 0 ? -q : q) + eta, s_e[j]);
             const sf h = sf_from_int(eta, s_e[j]);
 #pragma unroll
-            for (int s = M; s >= 1; --s) F[s] = sf_add(F[s], sf_add(sf_mul(ce, F[s - 1]), sf_mul(h, G[s - 1])));
+            for (int s = M; s >= 1; --s)
+              if (s >= lo && s <= hi) F[s] = sf_add(F[s], sf_add(sf_mul(ce, F[s - 1]), sf_mul(h, G[s - 1])));
           }
 #pragma unroll
-          for (int s = M; s >= 1; --s) G[s] = sf_add(G[s], sf_mul(c, G[s - 1]));
+          for (int s = M; s >= 1; --s)
+            if (s >= lo && s <= hi) G[s] = sf_add(G[s], sf_mul(c, G[s - 1]));
         }
         accumulate(b0, b1, b2, G[M], 0u);
         if (use_f) accumulate(f0, f1, f2, F[M], 0u);

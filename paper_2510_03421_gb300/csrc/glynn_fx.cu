@@ -217,6 +217,127 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) glynn_fx_kernel(Swee
   }
 }
 
+// The same sweep with a lane pair per term: lane 2p + h holds the column sums of
+// columns [h N/2, (h + 1) N/2) only, forms their product (the last K2 of them on the
+// FP64 unit), and the two half products are multiplied after one exchange between the
+// lanes (one more 64x64-bit high product, truncating by < 2^-62).  Half the column
+// sums per lane halves the registers, so twice as many warps are resident to hide
+// the latency of the product chains.  Both lanes of a pair hold the same term and
+// each adds half of it (one exponent less: exact in the 192-bit window).  The loop
+// runs the same number of steps on every lane (lanes past their range's end compute
+// but do not add), so the exchange always sees the whole warp.  No error-bound
+// variant: calls that ask for a bound take glynn_fx_kernel.
+template <int N, int K2, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) glynn_fxp_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
+  constexpr int H = N / 2;
+  static_assert(N % 4 == 0 && (H - K2) % 2 == 0, "halves of whole 16-byte rows, integer columns in pairs");
+  extern __shared__ __align__(16) long long smem_fx[];
+  __shared__ dd scratch[32];
+  const int n = a.n;
+  long long* sP = smem_fx;          // +2 q_ij
+  long long* sM = smem_fx + n * N;  // -2 q_ij
+  for (int idx = threadIdx.x; idx < n * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - i * N;
+    const long long v = (j < n) ? tab->d[i * 64 + j] : 0;
+    sP[idx] = v;
+    sM[idx] = -v;
+  }
+  const int e_sum = tab->e_sum + 31 * (N - n);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
+  const int j0 = half * H;  // first column of this lane
+  const uint64_t L = 1ull << a.chunk_log2;
+  const uint64_t c_first = a.g_begin >> a.chunk_log2;
+  const uint64_t c_end = (a.g_end + L - 1) >> a.chunk_log2;
+  const uint64_t rounds = (c_end - c_first + 15) / 16;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+
+  int e_lo = 0;
+  bool anchored = false;
+  u64 a0 = 0, a1 = 0, a2 = 0;
+  long long S[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) S[j] = 0;
+  for (uint64_t r = warp; r < rounds; r += warps) {  // uniform over the warp
+    const uint64_t chunk = c_first + 16 * r + pair;
+    uint64_t ga = chunk << a.chunk_log2, gb = ga + L;
+    if (ga < a.g_begin) ga = a.g_begin;
+    if (gb > a.g_end) gb = a.g_end;
+    if (chunk >= c_end) ga = gb = a.g_end;  // idle pair
+    for (uint64_t t = 0; t < L; ++t) {
+      const uint64_t g = ga + t;
+      const bool active = g < gb;  // the same on both lanes of a pair
+      if (active) {
+        if (t == 0) {
+          const uint64_t gray = g ^ (g >> 1);
+#pragma unroll
+          for (int j = 0; j < H; ++j) S[j] = 0;
+          for (int i = 0; i < n; ++i) {
+            const long long* row = (((gray >> (n - 1 - i)) & 1u) ? sM : sP) + i * N + j0;
+#pragma unroll
+            for (int j = 0; j < H; ++j) S[j] += row[j];
+          }
+#pragma unroll
+          for (int j = 0; j < H; ++j) S[j] = (j0 + j < n) ? (S[j] >> 1) : (1ll << 31);
+        } else {
+          const int b = ctz64(g);
+          const long long* row = (((g >> (b + 1)) & 1u) ? sP : sM) + (n - 1 - b) * N + j0;
+          // H is even, so a half row starts on a 16-byte boundary
+          const longlong2* row2 = reinterpret_cast<const longlong2*>(row);
+#pragma unroll
+          for (int j = 0; j < H / 2; ++j) {
+            const longlong2 v = row2[j];
+            S[2 * j] += v.x;
+            S[2 * j + 1] += v.y;
+          }
+        }
+      }
+      u64 P;
+      int E;
+      unsigned neg;
+      soft_product<H, K2, false>(S, P, E, neg);
+      // the partner's half product; each P is 0 or in [2^63, 2^64), value P 2^(E - 63)
+      const u64 Po = __shfl_xor_sync(0xffffffffu, P, 1);
+      const int Eo = __shfl_xor_sync(0xffffffffu, (int)(((unsigned)E << 1) | neg), 1);
+      const u64 h2 = __umul64hi(P, Po);  // P Po 2^(E + Eo - 126) ~ h2 2^(E + Eo - 62)
+      const int top = (int)(h2 >> 63);
+      P = top ? h2 : (h2 << 1);
+      E = E + (Eo >> 1) + top;
+      neg ^= (unsigned)Eo & 1u;
+      if (active && P != 0) {
+        // half of the term: P 2^(E - 1 - 63 - e_sum)
+        const int Eh = E - 1;
+        if (!anchored) {
+          e_lo = Eh - e_sum - kAnchorBit;
+          anchored = true;
+        }
+        int p = Eh - 63 - e_sum - e_lo;
+        if (p > kMaxLsb) {
+          shr192(a0, a1, a2, p - kMaxLsb);
+          e_lo += p - kMaxLsb;
+          p = kMaxLsb;
+        }
+        if (p >= 0)
+          acc_add_nb(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u));
+        else
+          acc_add(a0, a1, a2, P, p, neg ^ (unsigned)(g & 1u));
+      }
+    }
+  }
+  dd v[1] = {to_dd(a0, a1, a2, e_lo)};
+  block_sum_dd<1>(v, scratch);
+  if (threadIdx.x == 0) {
+    const bool bad = tab->bad != 0;
+    double* rec = static_cast<double*>(a.partials) + (size_t)blockIdx.x * kRealRecord;
+    rec[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v[0].hi;
+    rec[1] = bad ? 0.0 : v[0].lo;
+    rec[2] = 0.0;
+    rec[3] = 0.0;
+  }
+}
+
 // Columns multiplied on the FP64 unit by the mixed variant, per padded order: enough
 // to move a share of the work off the integer pipes, few enough that the FP64 unit
 // (2K - 1 operations per term at 1/74 of the integer rate) is not the bottleneck.
@@ -256,7 +377,40 @@ void* pick(int n, bool mixed, bool abs) {
 
 size_t smem_bytes(int n) { return 2u * (size_t)n * (size_t)((n + 3) & ~3) * sizeof(long long); }
 
+// Lane-pair kernel, from N = 40 (where the one-lane kernel holds 8 warps per SM):
+// 4 FP64 columns per half, 256 threads, two blocks per SM (16 warps, <= 128
+// registers; N = 52 would spill and stays on the one-lane kernel).  Measured on
+// GB300 against the one-lane kernel (terms/s): n = 40: 1.95e10 -> 2.11e10,
+// 44: 1.80e10 -> 1.92e10, 48: 1.77e10 -> 1.78e10, 56: 1.45e10 -> 1.52e10,
+// 64: 1.24e10 -> 1.29e10.  Below N = 40 it is slower (n = 28 / 32 / 36: -15%, -11%,
+// -13%): the pipes, not latency, bound the one-lane kernel there, and the pair adds
+// the exchange and a second accumulation per term.
+constexpr int kPairFp64Columns = 4;
+constexpr int kPairBlock = 256;
+constexpr int kPairMinBlocks = 2;
+
+template <int N>
+void* pair_kernel() {
+  return (void*)glynn_fxp_kernel<N, kPairFp64Columns, kPairBlock, kPairMinBlocks>;
+}
+
+void* pick_pair(int n) {
+  switch ((n + 3) & ~3) {
+    case 40: return pair_kernel<40>();
+    case 44: return pair_kernel<44>();
+    case 48: return pair_kernel<48>();
+    case 56: return pair_kernel<56>();
+    case 60: return pair_kernel<60>();
+    case 64: return pair_kernel<64>();
+    default: return nullptr;
+  }
+}
+
 }  // namespace
+
+bool glynn_fx_pair_available(int n) { return pick_pair(n) != nullptr; }
+int glynn_fx_pair_block() { return kPairBlock; }
+int glynn_fx_pair_mixed_columns(int) { return 2 * kPairFp64Columns; }
 
 // Threads per block: 192 (two blocks, 12 warps per SM, <= 168 registers) up to N = 36;
 // 128 above (two blocks, 8 warps, <= 255 registers: the column sums no longer fit 168).
@@ -267,8 +421,8 @@ int glynn_fx_mixed_columns(int n) {
   return N >= 40 ? 0 : mixed_columns(N);
 }
 
-int glynn_fx_blocks_per_sm(int n, int block, bool mixed) {
-  void* k = pick(n, mixed, false);
+int glynn_fx_blocks_per_sm(int n, int block, bool mixed, bool pair) {
+  void* k = pair ? pick_pair(n) : pick(n, mixed, false);
   if (!k) return 0;
   const size_t smem = smem_bytes(n);
   if (smem > 32 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -282,8 +436,10 @@ cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream
   return cudaGetLastError();
 }
 
-cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed) {
-  void* k = pick(a.n, mixed, want_abs);
+cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed,
+                            bool pair) {
+  if (pair && (want_abs || !mixed || c.block != kPairBlock)) return cudaErrorInvalidValue;
+  void* k = pair ? pick_pair(a.n) : pick(a.n, mixed, want_abs);
   if (!k) return cudaErrorInvalidValue;
   cudaError_t e = launch_fx_prep(a, tab, c.stream);
   if (e != cudaSuccess) return e;

@@ -55,10 +55,15 @@ struct FxTable {
 };
 // mixed: the last glynn_fx_mixed_columns(n) columns' product runs on the FP64 unit
 cudaError_t launch_fx_prep(const SweepArgs& a, FxTable* tab, cudaStream_t stream);
-cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed);
-int glynn_fx_blocks_per_sm(int n, int block, bool mixed);
+// pair: the lane-pair kernel (glynn_fxp_kernel; mixed, no error bound, its own block)
+cudaError_t launch_glynn_fx(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs, bool mixed,
+                            bool pair = false);
+int glynn_fx_blocks_per_sm(int n, int block, bool mixed, bool pair = false);
 int glynn_fx_mixed_columns(int n);
 int glynn_fx_block(int n);  // threads per block of the square kernel (its launch bound)
+bool glynn_fx_pair_available(int n);
+int glynn_fx_pair_block();               // threads per block of the lane-pair kernel
+int glynn_fx_pair_mixed_columns(int n);  // columns on the FP64 unit, both halves together
 // grouped rectangular walk (1 <= m < n; glynn_fxg.cu): g ranges over [0, 2^(m-1)),
 // n - m + 1 terms each
 cudaError_t launch_glynn_fxg(const SweepArgs& a, FxTable* tab, const LaunchCfg& c, bool want_abs);

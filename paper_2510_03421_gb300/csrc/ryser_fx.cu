@@ -12,7 +12,10 @@
 //     (fixed_common.cuh, pairs of rows), multiplied by the exact 64-bit binomial weight;
 //   * the signed terms go into a 192-bit fixed-point accumulator per thread.
 // Subsets with more than m columns (weight 0) and the empty subset cost only the row
-// update.  The error-bound variant (ABS) takes exact magnitudes, adds up sum |term|
+// update.  A whole sweep hands the chunks to the lanes in a size-coherent order (see
+// coherent_chunk): the 32 lanes of a warp then see the same subset size at every step,
+// so a warp skips the product together instead of paying for it whenever any lane
+// needs one, and chunks whose subsets all exceed m columns are skipped.  The error-bound variant (ABS) takes exact magnitudes, adds up sum |term|
 // and, when some entry was rounded to fixed point, the products of (|R_i| + n/2 units)
 // that bound the effect of that rounding.
 #include "device_common.cuh"
@@ -69,6 +72,43 @@ __global__ void ryser_fx_prep_kernel(SweepArgs a, FxTable* tab) {
   }
 }
 
+// Chunk of work item `item` in the size-coherent order: chunk c = gray^-1(x) where x runs
+// over the (nb)-bit numbers by popcount h (h = 0, 1, ...) and, within one popcount, in
+// colex order (combinatorial number system).  For g in chunk c (chunks of 2^k terms)
+// the bits of gray(g) above k - 1 are those of gray(c) = x, and bit k - 1 is c_0 ^ g_{k-1}
+// with c_0 = parity of x = h mod 2; so lanes holding chunks of one popcount h see the
+// same subset size at every step.  cum[h] = number of items of popcount < h.
+__device__ __forceinline__ uint64_t coherent_chunk(uint64_t item, int nb, const unsigned long long* cum, int* h_out) {
+  int h = 0;
+  while (h < nb && cum[h + 1] <= item) ++h;
+  unsigned long long t = item - cum[h];
+  // colex unranking: the largest p with C(p, i) <= t holds element i, for i = h .. 1
+  unsigned __int128 b = 1;  // C(nb - 1, h)
+  for (int q = 1; q <= h; ++q) b = b * (unsigned __int128)(nb - 1 - h + q) / (unsigned __int128)q;
+  uint64_t x = 0;
+  int i = h;
+  for (int p = nb - 1; p >= 0 && i > 0; --p) {
+    // b = C(p, i)
+    if ((unsigned __int128)t >= b) {
+      x |= 1ull << p;
+      t -= (unsigned long long)b;
+      b = p > 0 ? b * (unsigned __int128)i / (unsigned __int128)p : 0;  // C(p - 1, i - 1)
+      --i;
+    } else {
+      b = p > 0 ? b * (unsigned __int128)(p - i) / (unsigned __int128)p : 0;  // C(p - 1, i)
+    }
+  }
+  uint64_t c = x;  // inverse Gray code: prefix XOR from the top
+  c ^= c >> 1;
+  c ^= c >> 2;
+  c ^= c >> 4;
+  c ^= c >> 8;
+  c ^= c >> 16;
+  c ^= c >> 32;
+  *h_out = h;
+  return c;
+}
+
 template <int N, bool ABS>
 __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) ryser_fx_kernel(SweepArgs a, const FxTable* __restrict__ tab) {
   extern __shared__ long long smem_rf[];
@@ -90,6 +130,21 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) ryser_fx_kernel(Swee
       const int lz = __clzll((long long)c);
       s_wm[s] = c << lz;
       s_we[s] = 64 - lz;
+    }
+  }
+  // size-coherent chunk order for whole sweeps (start_mode == 1 from the host): cum[h] =
+  // sum_{h' < h} C(nb, h'), nb = n - chunk_log2 bits of chunk index
+  __shared__ unsigned long long s_cum[66];
+  const bool coherent = a.start_mode == 1;
+  const int nb = n - a.chunk_log2;
+  if (coherent && threadIdx.x == 0) {
+    unsigned long long run = 0, b = 1;  // b = C(nb, h)
+    for (int h = 0; h <= nb + 1 && h < 66; ++h) {
+      s_cum[h] = run;
+      if (h <= nb) {
+        run += b;
+        b = (unsigned long long)((unsigned __int128)b * (unsigned __int128)(nb - h) / (unsigned __int128)(h + 1));
+      }
     }
   }
   const int e_sum = tab->e_sum + 31 * (N - m);  // padded rows hold 2^31 = 1 * 2^31
@@ -143,11 +198,18 @@ __global__ void __launch_bounds__((N <= 36) ? 192 : 128, 2) ryser_fx_kernel(Swee
   long long R[N];
   int size = 0;
   for (uint64_t r = warp; r < rounds; r += warps) {
-    const uint64_t chunk = c_first + 32 * r + lane;
+    uint64_t chunk = c_first + 32 * r + lane;
+    bool skip = chunk >= c_end;
+    if (coherent && !skip) {
+      int h;
+      chunk = coherent_chunk(chunk, nb, s_cum, &h);
+      // every subset of the chunk has at least h columns: nothing to add above m
+      skip = h > m;
+    }
     uint64_t ga = chunk << a.chunk_log2, gb = ga + L;
     if (ga < a.g_begin) ga = a.g_begin;
     if (gb > a.g_end) gb = a.g_end;
-    if (chunk >= c_end) ga = gb = a.g_end;  // idle lane
+    if (skip) ga = gb = a.g_end;  // idle lane
     for (uint64_t g = ga; g < gb; ++g) {
       if (g == ga) {
         const uint64_t gray = g ^ (g >> 1);

@@ -161,6 +161,27 @@ def test_mixed_sampled_n36_against_oracle_partials(capi, dev):
         assert abs(got - ref) <= max(1e-13 * abs(ref), (33 * 2.0 ** -60 + 16 * 2.0 ** -53) * scale)
 
 
+@pytest.mark.parametrize("n", [37, 41, 47, 58, 64])
+def test_lane_pair_sweep_sampled_partials(capi, dev, n):
+    # from n = 37 the mixed sweep runs a lane pair per term (each lane half of the
+    # columns, 4 of them on the FP64 unit, one more truncated product to join the
+    # halves): ragged ranges and one crossing chunk boundaries, on the planned grid, one
+    # block, 7 blocks with 8-term chunks (pairs past the range's end), and the one-lane
+    # kernel (block = 128), against the oracle
+    import torch
+    A = inputs.uniform_real(n, n, 7660 + n)
+    T = 1 << (n - 1)
+    for a, b in ((0, 3000), (T // 3 + 5, T // 3 + 5000), (T - 2049, T)):
+        ref = oracle.glynn_partial(A, a, b)
+        scale = oracle.glynn_partial_abs(A, a, b)
+        tol = max(1e-13 * abs(ref), ((n - 8 + 6) * 2.0 ** -60 + 16 * 2.0 ** -53) * scale)
+        for opts in (MIXED, dict(MIXED, grid=1), dict(MIXED, grid=7, chunk_log2=3), dict(MIXED, block=128)):
+            out = capi.perm_glynn_partial(to_dev(A, dev), a, b, opts=opts)
+            torch.cuda.synchronize(dev)
+            got = capi.dd_value(out)
+            assert abs(got - ref) <= tol, (n, a, b, opts, abs(got - ref), "tol/|ref|", tol / abs(ref))
+
+
 # ------------------------------------------------- rectangles (m < n)
 _exact_cache = {}
 
