@@ -12,14 +12,18 @@
 // combined in a Kahan sum (real, complex) or modulo 2^128 (integer; Gaussian integers
 // per part).
 //
-// The last three rows: below a node with three rows left, the subtree's value depends
-// only on the set of free columns.  For n <= 16 (not for Gaussian integers) the block
-// first tabulates, for every column triple a < b < c, the sum of the six products
-// a_{r0 x} a_{r1 y} a_{r2 z} over the orderings (x, y, z) of (a, b, c) -- the same
-// leaf products the search would form -- and the search stops four rows early: for
-// each nonzero free column x of the fourth-last row it adds a_x times the table entries
-// of the triples of the remaining free columns.  That removes the four deepest levels
-// of the tree from the search, which hold all but a 24th of its nodes.
+// The last rows: below a node with r rows left, the subtree's value depends only on
+// the set of free columns.  For n <= 16 (not for Gaussian integers) the block first
+// tabulates, for every column triple S (colex rank x + C(y,2) + C(z,3), x < y < z),
+// the permanent of the last three rows on S -- the sum of the six leaf products the
+// search would form -- and, from m = 5, for every column quadruple the permanent of
+// the last four rows on it, formed from the triples' table the way the search
+// combines a row with the rows below (sum over c in S of a_{m-4,c} T3[S - c]).  The
+// search then stops five rows early: for each nonzero free column x of the fifth-last
+// row it adds a_x times the table entries of the quadruples of the remaining free
+// columns (one entry for a square).  That removes the five deepest levels of the tree
+// from the search, which hold all but a 120th of its nodes.  (With four or three
+// rows left at the prefix depth, the quadruple or triple sums are taken directly.)
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -104,33 +108,73 @@ __device__ __forceinline__ void kahan(double& acc, double& comp, double x) {
   acc = s;
 }
 
+constexpr int kTailN = 16;  // column count up to which the tail tables are built
+
+// C(c, k) for small c, k by the product formula (after step i, r = C(c, i + 1); exact),
+// without recursion so that the kernel's stack size stays statically known
+__host__ __device__ constexpr int binom_small(int c, int k) {
+  long long r = 1;
+  for (int i = 0; i < k; ++i) r = r * (c - i) / (i + 1);
+  return c < k ? 0 : (int)r;
+}
+
 template <class F>
 __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes, int tail) {
   typedef typename F::T T;
   extern __shared__ unsigned char smem_c[];
   __shared__ unsigned long long rowmask[kMaxN];
+  __shared__ int sB[5][kTailN + 1];  // sB[k][c] = C(c, k): colex ranks of column sets
   const int n = a.n, m = a.m;
   T* sA = reinterpret_cast<T*>(smem_c);  // sA[i * n + j]
-  T* sT = sA + m * n;                    // tail: sT[(x * n + y) * n + z], x < y < z
+  T* sT3 = sA + m * n;                   // last three rows on triple rank x + C(y,2) + C(z,3)
+  T* sT4 = sT3 + binom_small(kTailN, 3); // last four rows on quadruple rank ... + C(w,4)
+  const bool tail4 = tail && m >= 5;
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
     sA[idx] = F::load(a.A, i * a.rs + j * a.cs);
+  }
+  for (int idx = threadIdx.x; idx < 5 * (kTailN + 1); idx += blockDim.x) {
+    const int k = idx / (kTailN + 1), c = idx - k * (kTailN + 1);
+    sB[k][c] = binom_small(c, k);
   }
   __syncthreads();
   if (tail) {
     const T* r0 = sA + (m - 3) * n;
     const T* r1 = sA + (m - 2) * n;
     const T* r2 = sA + (m - 1) * n;
-    for (int idx = threadIdx.x; idx < n * n * n; idx += blockDim.x) {
-      const int x = idx / (n * n), y = (idx / n) % n, z = idx % n;
-      if (!(x < y && y < z)) continue;
+    for (int idx = threadIdx.x; idx < sB[3][n]; idx += blockDim.x) {
+      // colex unranking: z the largest column with C(z,3) <= idx, then y, then x
+      int rem = idx, z = 2, y = 1;
+      while (z + 1 < n && sB[3][z + 1] <= rem) ++z;
+      rem -= sB[3][z];
+      while (y + 1 < z && sB[2][y + 1] <= rem) ++y;
+      const int x = rem - sB[2][y];
       // the six orderings of (x, y, z) over rows r0, r1, r2
       T v = F::mul(r0[x], F::add(F::mul(r1[y], r2[z]), F::mul(r1[z], r2[y])));
       v = F::fma(r0[y], F::add(F::mul(r1[x], r2[z]), F::mul(r1[z], r2[x])), v);
       v = F::fma(r0[z], F::add(F::mul(r1[x], r2[y]), F::mul(r1[y], r2[x])), v);
-      sT[idx] = v;
+      sT3[idx] = v;
     }
     __syncthreads();
+    if (tail4) {
+      const T* r = sA + (m - 4) * n;
+      for (int idx = threadIdx.x; idx < sB[4][n]; idx += blockDim.x) {
+        int rem = idx, w = 3, z = 2, y = 1;
+        while (w + 1 < n && sB[4][w + 1] <= rem) ++w;
+        rem -= sB[4][w];
+        while (z + 1 < w && sB[3][z + 1] <= rem) ++z;
+        rem -= sB[3][z];
+        while (y + 1 < z && sB[2][y + 1] <= rem) ++y;
+        const int x = rem - sB[2][y];
+        // row m-4 on each column c of the quadruple, the last three rows on the rest
+        T v = F::mul(r[x], sT3[y + sB[2][z] + sB[3][w]]);
+        v = F::fma(r[y], sT3[x + sB[2][z] + sB[3][w]], v);
+        v = F::fma(r[z], sT3[x + sB[2][y] + sB[3][w]], v);
+        v = F::fma(r[w], sT3[x + sB[2][y] + sB[3][z]], v);
+        sT4[idx] = v;
+      }
+      __syncthreads();
+    }
   }
   const unsigned long long allcols = (n == 64) ? ~0ull : ((1ull << n) - 1);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -177,7 +221,7 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
       int k = depth;
       cand[k] = rowmask[k] & ~used;
       val[k] = F::zero();
-      // sum of the table entries over the triples of the column set fm
+      // sums of the table entries over the triples / quadruples of the column set fm
       auto triples = [&](unsigned long long fm) {
         T s = F::zero();
         unsigned long long xm = fm;
@@ -188,20 +232,62 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
           while (ym) {
             const int y = __ffsll((long long)ym) - 1;
             ym &= ym - 1;
+            const int rxy = x + sB[2][y];
             unsigned long long zm = ym;
             while (zm) {
               const int z = __ffsll((long long)zm) - 1;
               zm &= zm - 1;
-              s = F::add(s, sT[(x * n + y) * n + z]);
+              s = F::add(s, sT3[rxy + sB[3][z]]);
+            }
+          }
+        }
+        return s;
+      };
+      auto quadruples = [&](unsigned long long fm) {
+        T s = F::zero();
+        unsigned long long xm = fm;
+        while (xm) {
+          const int x = __ffsll((long long)xm) - 1;
+          xm &= xm - 1;
+          unsigned long long ym = xm;
+          while (ym) {
+            const int y = __ffsll((long long)ym) - 1;
+            ym &= ym - 1;
+            const int rxy = x + sB[2][y];
+            unsigned long long zm = ym;
+            while (zm) {
+              const int z = __ffsll((long long)zm) - 1;
+              zm &= zm - 1;
+              const int rxyz = rxy + sB[3][z];
+              unsigned long long wm = zm;
+              while (wm) {
+                const int w = __ffsll((long long)wm) - 1;
+                wm &= wm - 1;
+                s = F::add(s, sT4[rxyz + sB[4][w]]);
+              }
             }
           }
         }
         return s;
       };
       while (true) {
-        if (tail && k == m - 4) {
-          // four rows left: each nonzero free column x of row k times the table sum
+        if (tail4 && k == m - 5) {
+          // five rows left: each nonzero free column x of row k times the quadruple sum
           // over the rest, without descending
+          const unsigned long long fm = allcols & ~used;
+          unsigned long long xm = rowmask[k] & fm;
+          T s = F::zero();
+          while (xm) {
+            const int x = __ffsll((long long)xm) - 1;
+            xm &= xm - 1;
+            s = F::fma(sA[k * n + x], quadruples(fm & ~(1ull << x)), s);
+          }
+          val[k] = s;
+          cand[k] = 0;
+        } else if (tail4 && k == m - 4) {
+          val[k] = quadruples(allcols & ~used);
+          cand[k] = 0;
+        } else if (tail && k == m - 4) {
           const unsigned long long fm = allcols & ~used;
           unsigned long long xm = rowmask[k] & fm;
           T s = F::zero();
@@ -322,11 +408,13 @@ void* pick(int dtype) {
 
 size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : dtype == 4 ? 32 : 16; }
 
-// the table of the last three rows: n <= 16, at least four rows, not Gaussian integers
-bool use_tail(int m, int n, int dtype) { return n <= 16 && m >= 4 && dtype != 4; }
+// the tables of the last rows: n <= 16, at least four rows, not Gaussian integers
+// (room for C(16,3) triples and C(16,4) quadruples)
+bool use_tail(int m, int n, int dtype) { return n <= kTailN && m >= 4 && dtype != 4; }
 
 size_t smem_bytes(int m, int n, int dtype) {
-  const size_t cells = (size_t)m * n + (use_tail(m, n, dtype) ? (size_t)n * n * n : 0);
+  const size_t cells =
+      (size_t)m * n + (use_tail(m, n, dtype) ? (size_t)(binom_small(kTailN, 3) + binom_small(kTailN, 4)) : 0);
   return cells * elem_bytes(dtype);
 }
 

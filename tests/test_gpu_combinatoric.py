@@ -43,6 +43,23 @@ def test_sparse_real_16(capi, dev, density):
     close(run(capi, "perm_combinatoric", A, dev, dict(max_terms=1 << 62)), oracle.glynn(A), A, kind="definition")
 
 
+@pytest.mark.parametrize("m,n", [(9, 13), (11, 14), (12, 16)])
+def test_rectangular_tail_tables(capi, dev, m, n):
+    # below the prefix rows the search meets the tables of the last three and four rows
+    # with more free columns than rows left (sums over all triples / quadruples of the
+    # free columns): uniform[0,1] against the long-double Glynn (no cancellation there),
+    # a signed 9 x 13 against the exact value, and 0/1 input bit-exact
+    from oracle import exact
+    cap = dict(max_terms=1 << 46)
+    A = inputs.uniform_real(m, n, 8800 + 31 * m + n, 0.0, 1.0)
+    close(run(capi, "perm_combinatoric", A, dev, cap), oracle.glynn(A), A, kind="definition")
+    if m == 9:
+        S = inputs.uniform_real(m, n, 8850 + n)
+        close(run(capi, "perm_combinatoric", S, dev, cap), float(exact.glynn_rect_grouped(S)), S, kind="definition")
+    B = inputs.bernoulli01(m, n, 8900 + 31 * m + n, 0.5)
+    assert run(capi, "perm_combinatoric", B, dev, cap) == oracle.subset_dp(B.astype(np.int64))
+
+
 def test_transposed_and_complex(capi, dev):
     A = inputs.uniform_real(7, 4, 8301)
     close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A.T), A, kind="definition")
