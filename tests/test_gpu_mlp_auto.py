@@ -122,13 +122,14 @@ def test_ryser_partial_matches_oracle(capi, dev):
 
 def test_trained_model_gains_over_dispatch_without_it(capi, dev):
     # the shipped model was trained on this GPU type by costmodel.main (3,000 timed grid
-    # cells); score it on a fresh held-out batch against exhaustive timing
+    # cells); score it on a fresh held-out batch of 1,000 matrices against exhaustive
+    # timing (every candidate's median of 5, so that timing noise does not decide)
     from paper_2510_03421_gb300 import costmodel
     w, dims, meta = costmodel.load()
     assert dims == costmodel.DIMS
     rule = costmodel.PaperRule()
     rule.p = np.array(meta["paper_rule"])
-    res = costmodel.evaluate(dev, w, rule, 400, 9961, reps=3)
+    res = costmodel.evaluate(dev, w, rule, 1000, 9961, reps=5)
     r = res["ratio_to_exhaustive"]
     print(res)
     assert r["model"] < min(r["always_glynn"], r["builtin"], r["paper_rule"])
