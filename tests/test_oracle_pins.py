@@ -293,6 +293,28 @@ def test_focus_pointer_is_reflected_gray_code(n):
         assert flips == [3, 2, 3, 1, 3, 2, 3]
 
 
+def test_single_terms_follow_the_focus_pointer_order():
+    # term g of the partial sums is the g-th term of the algorithm: starting from all
+    # +1, the flips of Algorithm "Glynn's Algorithm for Square Matrices" at n = 4 hit
+    # rows 3, 2, 3, 1, 3, 2, 3, and term g carries the sign (-1)^g.  For a rank-one
+    # A = u v^T every column sum of a term is (u . delta) v_j, so each single term is
+    # (-1)^g (u . delta_g)^4 prod_j v_j: a wrong row per Gray bit or a wrong sign
+    # changes the single terms even where the full sum is unchanged.
+    u = np.array([1.0, 2.0, 5.0, 11.0])
+    v = np.array([1.0, 3.0, -2.0, 7.0])
+    A = np.outer(u, v)
+    delta = np.ones(4)
+    deltas = [delta.copy()]
+    for row in [3, 2, 3, 1, 3, 2, 3]:
+        delta[row] = -delta[row]
+        deltas.append(delta.copy())
+    for g, d in enumerate(deltas):
+        term = (-1) ** g * float(u @ d) ** 4 * float(np.prod(v))
+        assert oracle.glynn_partial(A, g, g + 1) == term, g
+        assert oracle.glynn_partial(A.astype(np.int64), g, g + 1) == int(term), g
+        assert oracle.glynn_partial(A * (1 + 1j), g, g + 1) == term * (1 + 1j) ** 4, g
+
+
 @pytest.mark.parametrize("m,n,kind", [(5, 5, "real"), (4, 7, "real"), (6, 6, "complex"), (3, 8, "complex"),
                                       (7, 7, "int"), (4, 9, "int")])
 def test_glynn_partial_sums_the_same_terms(m, n, kind):
