@@ -1,10 +1,11 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake in a
 temporary copy of the oracle's C source -- a dropped term, a wrong sign, a wrong row
 per Gray-code bit, a wrong binomial weight or normalisation, an off-by-one range, a
-missing absolute value, a conjugated entry -- builds the copy with gcc, and runs the
-pin tests (test_oracle_pins.py) against it in a separate process.  Every mutant must
-make a pin fail; the unmodified copy must pass them all.  Nothing outside the
-temporary directory is changed."""
+missing absolute value, a conjugated entry, a transposed matrix -- in the C source or
+in the Python modules (scales, int128 decoding, the exact and rational oracles),
+builds the copy with gcc, and runs the pin tests (test_oracle_pins.py) against it in
+a separate process.  Every mutant must make a pin fail; the unmodified copy must pass
+them all.  Nothing outside the temporary directory is changed."""
 import concurrent.futures as cf
 import os
 import shutil
@@ -17,6 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 INC, C = "oracle_real.inc", "perm_oracle.c"
+PY, EXACT, CAUCHY = "__init__.py", "exact.py", "cauchy.py"
 
 # (name, file, text, replacement): the first occurrence of `text` is replaced
 MUTANTS = [
@@ -79,6 +81,21 @@ MUTANTS = [
     ("exact definition drops the maps with sigma(0) = 0", C,
      "    if (used[j]) continue;\n    used[j] = 1;\n    sigma[i] = j;\n    def_rec_i(",
      "    if (used[j] || (i == 0 && j == 0)) continue;\n    used[j] = 1;\n    sigma[i] = j;\n    def_rec_i("),
+    # the Python side: normalisations, the int128 decoding, the exact and rational oracles
+    ("sum of |term| scale divided by 2^n", PY, "return s / (2.0 ** (n - 1)) /", "return s / (2.0 ** n) /"),
+    ("closed-form scale divided by 2^m", PY, "/ 2.0 ** (m - 1)", "/ 2.0 ** m"),
+    ("int128 results read without their sign", PY, "return v - (1 << 128) if v >> 127 else v", "return v"),
+    ("per(|A|) of the real parts", PY, "A = np.abs(np.asarray(A)).astype(np.float64)",
+     "A = np.real(np.asarray(A)).astype(np.float64)"),
+    ("SBP selection matrix transposed", PY, "            P[j, k] = 1\n", "            P[k, j] = 1\n"),
+    ("exact complex definition with a wrong product sign", EXACT,
+     "pr, pi = pr * ar - pi * ai, pr * ai + pi * ar", "pr, pi = pr * ar + pi * ai, pr * ai + pi * ar"),
+    ("exact grouped Glynn: padding shift off its scale", EXACT, "shift = (k - 2 * t) * one", "shift = (k - 2 * t)"),
+    ("exact determinant ignores row swaps", CAUCHY, "            d = -d\n", ""),
+    ("Borchardt without the Hadamard square", CAUCHY, "CC = [[c * c for c in row] for row in C]",
+     "CC = [[c for c in row] for row in C]"),
+    ("Cauchy determinant closed form with a flipped factor", CAUCHY, "num *= (X[j] - X[i]) * (Y[i] - Y[j])",
+     "num *= (X[j] - X[i]) * (Y[j] - Y[i])"),
 ]
 
 RUNNER = """
