@@ -2,9 +2,10 @@
 temporary copy of the oracle's C source -- a dropped term, a wrong sign, a wrong row
 per Gray-code bit, a wrong binomial weight or normalisation, an off-by-one range, a
 missing absolute value, a conjugated entry, a transposed matrix -- in the C source or
-in the Python modules (scales, int128 decoding, the exact and rational oracles),
-builds the copy with gcc, and runs the pin tests (test_oracle_pins.py) against it in
-a separate process.  Every mutant must make a pin fail; the unmodified copy must pass
+in the Python modules (scales, int128 decoding, the exact and rational oracles, the
+cost model's reference perceptron),
+builds the copy with gcc, and runs the pin tests (test_oracle_pins.py,
+test_oracle_mlp.py) against it in a separate process.  Every mutant must make a pin fail; the unmodified copy must pass
 them all.  Nothing outside the temporary directory is changed."""
 import concurrent.futures as cf
 import os
@@ -16,9 +17,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
-PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_mlp.py")]
 INC, C = "oracle_real.inc", "perm_oracle.c"
-PY, EXACT, CAUCHY = "__init__.py", "exact.py", "cauchy.py"
+PY, EXACT, CAUCHY, MLP = "__init__.py", "exact.py", "cauchy.py", "mlp_ref.py"
 
 # (name, file, text, replacement): the first occurrence of `text` is replaced
 MUTANTS = [
@@ -96,6 +97,13 @@ MUTANTS = [
      "CC = [[c for c in row] for row in C]"),
     ("Cauchy determinant closed form with a flipped factor", CAUCHY, "num *= (X[j] - X[i]) * (Y[i] - Y[j])",
      "num *= (X[j] - X[i]) * (Y[j] - Y[i])"),
+    # the reference perceptron of the cost model
+    ("MLP gradient without the first ReLU mask", MLP, "d1 = (d2 @ W2.T) * (z1 > 0)", "d1 = d2 @ W2.T"),
+    ("MLP weight gradient transposed", MLP, "gW2 = a1.T @ d2", "gW2 = d2.T @ a1"),
+    ("MLP loss without the mask normalisation", MLP, "return float(np.sum(mask * (y - T) ** 2) / np.sum(mask))",
+     "return float(np.sum(mask * (y - T) ** 2))"),
+    ("MLP bias added after the activation", MLP, "    z1 = X @ W1 + b1\n    a1 = np.maximum(z1, 0.0)\n",
+     "    z1 = X @ W1\n    a1 = np.maximum(z1, 0.0) + b1\n"),
 ]
 
 RUNNER = """
@@ -106,7 +114,7 @@ assert oracle.__file__.startswith(sys.argv[1]), oracle.__file__
 oracle.build(force=True)
 print("BUILT", flush=True)
 import pytest
-sys.exit(int(pytest.main(["-x", "-q", "-p", "no:cacheprovider", sys.argv[2]])))
+sys.exit(int(pytest.main(["-x", "-q", "-p", "no:cacheprovider"] + sys.argv[2:])))
 """
 
 
@@ -125,7 +133,7 @@ def _copy_with(tmp, mutant):
 
 
 def _run(tmp):
-    p = subprocess.run([sys.executable, "-c", RUNNER, tmp, PINS], cwd=ROOT, capture_output=True, text=True,
+    p = subprocess.run([sys.executable, "-c", RUNNER, tmp] + PINS, cwd=ROOT, capture_output=True, text=True,
                        timeout=600)
     return p.returncode, p.stdout + p.stderr
 
