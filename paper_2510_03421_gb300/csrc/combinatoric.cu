@@ -21,8 +21,9 @@
 // combines a row with the rows below (sum over c in S of a_{m-4,c} T3[S - c]).  The
 // search then stops five rows early: for each nonzero free column x of the fifth-last
 // row it adds a_x times the table entries of the quadruples of the remaining free
-// columns (one entry for a square).  That removes the five deepest levels of the tree
-// from the search, which hold all but a 120th of its nodes.  (With four or three
+// columns (one entry for a square, found directly from the colex ranks of the five
+// free columns).  That removes the five deepest levels of the tree from the search,
+// which hold all but a 120th of its nodes.  (With four or three
 // rows left at the prefix depth, the quadruple or triple sums are taken directly.)
 #include <type_traits>
 
@@ -277,10 +278,31 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
           const unsigned long long fm = allcols & ~used;
           unsigned long long xm = rowmask[k] & fm;
           T s = F::zero();
-          while (xm) {
-            const int x = __ffsll((long long)xm) - 1;
-            xm &= xm - 1;
-            s = F::fma(sA[k * n + x], quadruples(fm & ~(1ull << x)), s);
+          if (__popcll(fm) == 5) {
+            // five free columns c0 < .. < c4 (a square): the rest of c_i is one quadruple,
+            // colex rank sum_j C(d_j, j + 1) over the other four in increasing order
+            unsigned long long r = fm;
+            int c[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+              c[q] = __ffsll((long long)r) - 1;
+              r &= r - 1;
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              if (!((xm >> c[i]) & 1ull)) continue;
+              int rank = 0, j = 1;
+#pragma unroll
+              for (int q = 0; q < 5; ++q)
+                if (q != i) rank += sB[j++][c[q]];
+              s = F::fma(sA[k * n + c[i]], sT4[rank], s);
+            }
+          } else {
+            while (xm) {
+              const int x = __ffsll((long long)xm) - 1;
+              xm &= xm - 1;
+              s = F::fma(sA[k * n + x], quadruples(fm & ~(1ull << x)), s);
+            }
           }
           val[k] = s;
           cand[k] = 0;

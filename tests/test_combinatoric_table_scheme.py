@@ -1,8 +1,9 @@
 """The tail-table scheme of the combinatoric kernel (csrc/combinatoric.cu), run on the
 CPU in exact integers: the colex ranks and unranking of column triples and
 quadruples, the tables of the last three and four rows built from each other, the
-prefix unranking of the first `depth` rows, and the search's branches with five,
-four or three rows left.  Checked against the definition (Eq.
+prefix unranking of the first `depth` rows, and the search's branches with five
+(the direct path for five free columns, and the general one), four or three rows
+left.  Checked against the definition (Eq.
 rectangular_permanent_definition) by brute force, for every prefix depth, with every
 table index asserted in bounds.  This pins the indexing the kernel relies on; the
 kernel itself is checked on the GPU (test_gpu_combinatoric.py)."""
@@ -93,6 +94,15 @@ def kernel_scheme(A, m, n, depth):
     def value(k, used):  # the search below row k with the columns `used` taken
         fm = allcols & ~used
         if tail4 and k == m - 5:
+            if bin(fm).count("1") == 5:  # a square: the rest of each free column is one quadruple
+                c = bits(fm)
+                s = 0
+                for i in range(5):
+                    if (rowmask[k] >> c[i]) & 1:
+                        r = rank(tuple(c[q] for q in range(5) if q != i))
+                        assert 0 <= r < comb(n, 4)
+                        s += A[k][c[i]] * T4[r]
+                return s
             return sum(A[k][x] * table_sum(T4, 4, n, fm & ~(1 << x)) for x in bits(rowmask[k] & fm))
         if tail4 and k == m - 4:
             return table_sum(T4, 4, n, fm)
