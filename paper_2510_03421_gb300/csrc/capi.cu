@@ -1,6 +1,7 @@
 // C ABI of libperm: argument checks, the transpose rule, host/device staging,
 // the launch planner and the dispatch to the kernel families (perm_auto and the cost
 // model: capi_auto.cu).
+#include <algorithm>
 #include <new>
 
 #include "capi_internal.h"
@@ -691,8 +692,8 @@ int combinatoric_run(Call& c) {
   for (int k = 0; k < c.m; ++k) leaves *= (long double)(c.n - k);
   const uint64_t cap = c.o.max_terms ? c.o.max_terms : (1ull << 44);
   if (leaves > (long double)cap) return PERM_ETOOBIG;
-  const int block = 128;
-  if (c.o.block > 128) return PERM_EINVAL;
+  const int block = combinatoric_block(c.m, c.n, c.dtype);
+  if (c.o.block > block) return PERM_EINVAL;
   int bps = combinatoric_blocks_per_sm(c.m, c.n, c.dtype, c.o.block ? c.o.block : block);
   const size_t rec = (c.dtype == PERM_F64)    ? kRealRecord * 8
                      : (c.dtype == PERM_C128) ? kCplxRecord * 8
@@ -702,7 +703,11 @@ int combinatoric_run(Call& c) {
   const uint64_t threads = (uint64_t)lc.grid * lc.block;
   int depth = 0;
   uint64_t prefixes = 1;
-  while (depth < c.m && prefixes < 8 * threads) {
+  // at most down to the level above the first table level (below it a prefix would be
+  // one table step, and unranking it would cost more than the step)
+  const int max_depth = std::max(c.m - combinatoric_table_rows(c.m, c.n, c.dtype) - 1, 0);
+  const int depth_cap = combinatoric_table_rows(c.m, c.n, c.dtype) ? max_depth : c.m;
+  while (depth < depth_cap && prefixes < 8 * threads) {
     prefixes *= (uint64_t)(c.n - depth);
     ++depth;
   }

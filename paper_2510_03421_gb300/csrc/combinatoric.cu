@@ -16,15 +16,15 @@
 // the set of free columns.  For n <= 16 (not for Gaussian integers) the block first
 // tabulates, for every column triple S (colex rank x + C(y,2) + C(z,3), x < y < z),
 // the permanent of the last three rows on S -- the sum of the six leaf products the
-// search would form -- and, from m = 5, for every column quadruple the permanent of
-// the last four rows on it, formed from the triples' table the way the search
-// combines a row with the rows below (sum over c in S of a_{m-4,c} T3[S - c]).  The
-// search then stops five rows early: for each nonzero free column x of the fifth-last
-// row it adds a_x times the table entries of the quadruples of the remaining free
-// columns (one entry for a square, found directly from the colex ranks of the five
-// free columns).  That removes the five deepest levels of the tree from the search,
-// which hold all but a 120th of its nodes.  (With four or three
-// rows left at the prefix depth, the quadruple or triple sums are taken directly.)
+// search would form -- from m = 5, for every column quadruple, the permanent of the
+// last four rows on it, formed from the triples' table the way the search combines a
+// row with the rows below (sum over c in S of a_{m-4,c} T3[S - c]), and, for real
+// input from m = 6, the same for the last five rows on every quintuple.  The search
+// stops where the tables take over: with six free columns (a square) each nonzero
+// free column of the sixth-last row times the five-row entry of the other five, found
+// from their colex ranks; otherwise with five rows left, each free column times the
+// four-row entries of the rest (one entry for a square).  The tables remove the five
+// or six deepest levels of the tree, which hold all but a 120th (720th) of its nodes.
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -120,21 +120,23 @@ __host__ __device__ constexpr int binom_small(int c, int k) {
 }
 
 template <class F>
-__global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes, int tail) {
+__global__ void __launch_bounds__(256) combinatoric_kernel(SweepArgs a, int depth, uint64_t prefixes, int tail) {
   typedef typename F::T T;
   extern __shared__ unsigned char smem_c[];
   __shared__ unsigned long long rowmask[kMaxN];
-  __shared__ int sB[5][kTailN + 1];  // sB[k][c] = C(c, k): colex ranks of column sets
+  __shared__ int sB[6][kTailN + 1];  // sB[k][c] = C(c, k): colex ranks of column sets
   const int n = a.n, m = a.m;
   T* sA = reinterpret_cast<T*>(smem_c);  // sA[i * n + j]
-  T* sT3 = sA + m * n;                   // last three rows on triple rank x + C(y,2) + C(z,3)
-  T* sT4 = sT3 + binom_small(kTailN, 3); // last four rows on quadruple rank ... + C(w,4)
+  T* sT3 = sA + m * n;              // last three rows on triple rank x + C(y,2) + C(z,3)
+  T* sT4 = sT3 + binom_small(n, 3); // last four rows on quadruple rank ... + C(w,4)
+  T* sT5 = sT4 + binom_small(n, 4); // last five rows on quintuple rank (tail == 2)
   const bool tail4 = tail && m >= 5;
+  const bool tail5 = tail == 2 && m >= 6;
   for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
     sA[idx] = F::load(a.A, i * a.rs + j * a.cs);
   }
-  for (int idx = threadIdx.x; idx < 5 * (kTailN + 1); idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < 6 * (kTailN + 1); idx += blockDim.x) {
     const int k = idx / (kTailN + 1), c = idx - k * (kTailN + 1);
     sB[k][c] = binom_small(c, k);
   }
@@ -176,6 +178,33 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
       }
       __syncthreads();
     }
+    if (tail5) {
+      const T* r = sA + (m - 5) * n;
+      for (int idx = threadIdx.x; idx < sB[5][n]; idx += blockDim.x) {
+        int c[5];
+        int rem = idx, top = n;
+#pragma unroll
+        for (int j = 5; j >= 1; --j) {  // colex unranking, largest element first
+          int p = j - 1;
+          while (p + 1 < top && sB[j][p + 1] <= rem) ++p;
+          rem -= sB[j][p];
+          c[j - 1] = p;
+          top = p;
+        }
+        // row m-5 on each column of the quintuple, the last four rows on the rest
+        T v = F::zero();
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          int rank = 0, j = 1;
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+            if (q != i) rank += sB[j++][c[q]];
+          v = (i == 0) ? F::mul(r[c[0]], sT4[rank]) : F::fma(r[c[i]], sT4[rank], v);
+        }
+        sT5[idx] = v;
+      }
+      __syncthreads();
+    }
   }
   const unsigned long long allcols = (n == 64) ? ~0ull : ((1ull << n) - 1);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -196,15 +225,24 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
 
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < prefixes; r += stride) {
-    // unrank the prefix
+    // unrank the prefix (in 32-bit arithmetic when every prefix index fits: 64-bit
+    // division by a run-time radix costs several times more)
     uint64_t rem = r;
+    unsigned rem32 = (unsigned)r;
+    const bool narrow = prefixes <= 0xffffffffull;
     unsigned long long used = 0;
     T pre = F::one();
     bool zero = false;
     for (int k = 0; k < depth; ++k) {
       const int radix = n - k;
-      int digit = (int)(rem % (uint64_t)radix);
-      rem /= (uint64_t)radix;
+      int digit;
+      if (narrow) {
+        digit = (int)(rem32 % (unsigned)radix);
+        rem32 /= (unsigned)radix;
+      } else {
+        digit = (int)(rem % (uint64_t)radix);
+        rem /= (uint64_t)radix;
+      }
       unsigned long long freecols = ~used & ((n == 64) ? ~0ull : ((1ull << n) - 1));
       for (int t = 0; t < digit; ++t) freecols &= freecols - 1;
       const int c = __ffsll((long long)freecols) - 1;
@@ -272,7 +310,31 @@ __global__ void __launch_bounds__(128) combinatoric_kernel(SweepArgs a, int dept
         return s;
       };
       while (true) {
-        if (tail4 && k == m - 5) {
+        if (tail5 && k == m - 6 && __popcll(allcols & ~used) == 6) {
+          // six rows left with six free columns (a square): each nonzero free column
+          // c_i of row k times the table entry of the other five, by their colex rank
+          const unsigned long long fm = allcols & ~used;
+          const unsigned long long xm = rowmask[k] & fm;
+          unsigned long long r = fm;
+          int c[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            c[q] = __ffsll((long long)r) - 1;
+            r &= r - 1;
+          }
+          T s = F::zero();
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            if (!((xm >> c[i]) & 1ull)) continue;
+            int rank = 0, j = 1;
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+              if (q != i) rank += sB[j++][c[q]];
+            s = F::fma(sA[k * n + c[i]], sT5[rank], s);
+          }
+          val[k] = s;
+          cand[k] = 0;
+        } else if (tail4 && k == m - 5) {
           // five rows left: each nonzero free column x of row k times the quadruple sum
           // over the rest, without descending
           const unsigned long long fm = allcols & ~used;
@@ -434,13 +496,30 @@ size_t elem_bytes(int dtype) { return dtype == 0 ? 8 : dtype == 4 ? 32 : 16; }
 // (room for C(16,3) triples and C(16,4) quadruples)
 bool use_tail(int m, int n, int dtype) { return n <= kTailN && m >= 4 && dtype != 4; }
 
+// the table of the last five rows as well: real input (8-byte entries, 54 KB of tables
+// in all at n = 16, shared by the 8 warps of a 256-thread block; 16-byte entries would
+// leave one block per SM) with m >= 6
+bool use_tail5(int m, int n, int dtype) { return use_tail(m, n, dtype) && m >= 6 && dtype == 0; }
+
 size_t smem_bytes(int m, int n, int dtype) {
-  const size_t cells =
-      (size_t)m * n + (use_tail(m, n, dtype) ? (size_t)(binom_small(kTailN, 3) + binom_small(kTailN, 4)) : 0);
+  size_t cells = (size_t)m * n;
+  if (use_tail(m, n, dtype)) cells += (size_t)(binom_small(n, 3) + binom_small(n, 4));
+  if (use_tail5(m, n, dtype)) cells += (size_t)binom_small(n, 5);
   return cells * elem_bytes(dtype);
 }
 
 }  // namespace
+
+// threads per block: 256 for real input with the five-row table (one copy of the tables
+// for 8 warps), else 128 (the integer and Gaussian reductions hold 128 partials)
+int combinatoric_block(int m, int n, int dtype) { return use_tail5(m, n, dtype) ? 256 : 128; }
+
+// rows below the search taken from the tables (five, four with only the four-row table,
+// none without tables): the prefix depth stays above them, so that every prefix still
+// has a level of the search below it
+int combinatoric_table_rows(int m, int n, int dtype) {
+  return use_tail5(m, n, dtype) ? 6 : (use_tail(m, n, dtype) && m >= 5) ? 5 : use_tail(m, n, dtype) ? 4 : 0;
+}
 
 int combinatoric_blocks_per_sm(int m, int n, int dtype, int block) {
   void* k = pick(dtype);
@@ -464,7 +543,7 @@ cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64
   SweepArgs args = a;
   int d = depth;
   uint64_t p = prefixes;
-  int t = use_tail(a.m, a.n, dtype) ? 1 : 0;
+  int t = use_tail5(a.m, a.n, dtype) ? 2 : use_tail(a.m, a.n, dtype) ? 1 : 0;
   void* params[] = {&args, &d, &p, &t};
   return cudaLaunchKernel(k, dim3(c.grid), dim3(c.block), params, smem, c.stream);
 }

@@ -163,6 +163,8 @@ int ryser_f64_blocks_per_sm(int m, int n, int block, bool weighted, bool want_ab
 
 // --- combinatoric algorithm (combinatoric.cu); dtype as perm_dtype
 cudaError_t launch_combinatoric(const SweepArgs& a, int dtype, int depth, uint64_t prefixes, const LaunchCfg& c);
+int combinatoric_block(int m, int n, int dtype);  // threads per block of the combinatoric kernel
+int combinatoric_table_rows(int m, int n, int dtype);  // rows from the first table level down
 int combinatoric_blocks_per_sm(int m, int n, int dtype, int block);
 
 // --- batched Glynn (batched.cu)

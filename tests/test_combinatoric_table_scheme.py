@@ -1,9 +1,9 @@
 """The tail-table scheme of the combinatoric kernel (csrc/combinatoric.cu), run on the
 CPU in exact integers: the colex ranks and unranking of column triples and
-quadruples, the tables of the last three and four rows built from each other, the
-prefix unranking of the first `depth` rows, and the search's branches with five
-(the direct path for five free columns, and the general one), four or three rows
-left.  Checked against the definition (Eq.
+quadruples and quintuples, the tables of the last three, four and five rows built
+from each other, the prefix unranking of the first `depth` rows, and the search's
+branches with six rows left (six free columns), five (the direct path for five free
+columns, and the general one), four or three.  Checked against the definition (Eq.
 rectangular_permanent_definition) by brute force, for every prefix depth, with every
 table index asserted in bounds.  This pins the indexing the kernel relies on; the
 kernel itself is checked on the GPU (test_gpu_combinatoric.py)."""
@@ -43,9 +43,10 @@ def rank(cols):
     return sum(comb(c, j + 1) for j, c in enumerate(cols))
 
 
-def tables(A, m, n):
+def tables(A, m, n, five):
     T3 = [None] * comb(TAIL_N, 3)
     T4 = [None] * comb(TAIL_N, 4)
+    T5 = [None] * comb(TAIL_N, 5)
     r0, r1, r2 = A[m - 3], A[m - 2], A[m - 1]
     for idx in range(comb(n, 3)):
         x, y, z = unrank(idx, 3, n)
@@ -62,7 +63,18 @@ def tables(A, m, n):
                 assert 0 <= i < comb(n, 3)
                 v += r[c] * T3[i]
             T4[idx] = v
-    return T3, T4
+    if five and m >= 6:
+        r = A[m - 5]
+        for idx in range(comb(n, 5)):
+            q = unrank(idx, 5, n)
+            assert all(0 <= a < b < n for a, b in zip(q, q[1:])) and rank(q) == idx
+            v = 0
+            for c in q:
+                i = rank(tuple(d for d in q if d != c))
+                assert 0 <= i < comb(n, 4)
+                v += r[c] * T4[i]
+            T5[idx] = v
+    return T3, T4, T5
 
 
 def table_sum(T, k, n, fm):
@@ -84,15 +96,25 @@ def _subsets(cols, k):
             yield (cols[j],) + rest
 
 
-def kernel_scheme(A, m, n, depth):
+def kernel_scheme(A, m, n, depth, five):
     tail = n <= TAIL_N and m >= 4
     tail4 = tail and m >= 5
-    T3, T4 = tables(A, m, n) if tail else (None, None)
+    tail5 = tail and five and m >= 6  # the kernel builds the five-row table for real input
+    T3, T4, T5 = tables(A, m, n, five) if tail else (None, None, None)
     allcols = (1 << n) - 1
     rowmask = [sum(1 << j for j in range(n) if A[i][j] != 0) for i in range(m)]
 
     def value(k, used):  # the search below row k with the columns `used` taken
         fm = allcols & ~used
+        if tail5 and k == m - 6 and bin(fm).count("1") == 6:  # a square: one quintuple each
+            c = bits(fm)
+            s = 0
+            for i in range(6):
+                if (rowmask[k] >> c[i]) & 1:
+                    r = rank(tuple(c[q] for q in range(6) if q != i))
+                    assert 0 <= r < comb(n, 5)
+                    s += A[k][c[i]] * T5[r]
+            return s
         if tail4 and k == m - 5:
             if bin(fm).count("1") == 5:  # a square: the rest of each free column is one quadruple
                 c = bits(fm)
@@ -132,7 +154,7 @@ def definition(A, m, n):
     return sum(prod(A[i][p[i]] for i in range(m)) for p in permutations(range(n), m))
 
 
-@pytest.mark.parametrize("m", range(1, 9))
+@pytest.mark.parametrize("m", range(1, 10))
 def test_tail_tables_match_definition_at_every_depth(m):
     rnd = random.Random(4200 + m)
     for n in range(m, min(m + 4, 10)):
@@ -140,11 +162,12 @@ def test_tail_tables_match_definition_at_every_depth(m):
         ref = definition(A, m, n)
         for depth in range(m + 1):
             if factorial(n) // factorial(n - depth) <= 20000:
-                assert kernel_scheme(A, m, n, depth) == ref, (m, n, depth)
+                for five in (False, True):
+                    assert kernel_scheme(A, m, n, depth, five) == ref, (m, n, depth, five)
 
 
 def test_colex_unranking_is_a_bijection_up_to_16_columns():
-    for k in (3, 4):
+    for k in (3, 4, 5):
         for n in range(k, TAIL_N + 1):
             got = [unrank(i, k, n) for i in range(comb(n, k))]
             assert len(set(got)) == comb(n, k)
