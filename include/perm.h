@@ -126,7 +126,10 @@ int perm_ryser(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, i
 
 /* The combinatoric algorithm: the definition (Eq. rectangular_permanent_definition)
  * summed over all m-permutations with shared prefix products; zero entries prune
- * whole subtrees.  Cost O(m n!/(n-m)!) on dense input; all dtypes. */
+ * whole subtrees.  For n <= 16 (not PERM_CI64) the last three to five rows come from
+ * per-block tables of their permanents on every column subset, so the search stops
+ * that many levels early.  Cost O(m n!/(n-m)!) on dense input (the tables divide it by
+ * up to 6!); opts->max_terms (default 2^44) caps the dense count n!/(n-m)!; all dtypes. */
 int perm_combinatoric(perm_handle h, const void* A, int64_t m, int64_t n, int64_t ld, int dtype, void* out,
                       void* stream, const perm_opts* opts);
 
