@@ -60,6 +60,24 @@ def test_rectangular_tail_tables(capi, dev, m, n):
     assert run(capi, "perm_combinatoric", B, dev, cap) == oracle.subset_dp(B.astype(np.int64))
 
 
+@pytest.mark.parametrize("opts", [dict(block=64, grid=3), dict(block=256, grid=1), dict(block=96, grid=7),
+                                  dict(block=32, grid=152)])
+def test_launch_shapes(capi, dev, opts):
+    # the tables are built by every block and the prefixes spread over a grid-stride
+    # loop: user block and grid sizes (real input takes up to 256 threads, the others
+    # up to 128) must give the same sum; 12x12 real with the five-row table, 9x11
+    # complex (four rows), 10x10 0/1 (int128)
+    A = inputs.uniform_real(12, 12, 8961)
+    close(run(capi, "perm_combinatoric", A, dev, opts), oracle.glynn(A), A, kind="definition")
+    small = dict(opts, block=min(opts["block"], 128))
+    C = inputs.complex_gaussian(9, 11, 8962)
+    close(run(capi, "perm_combinatoric", C, dev, small), oracle.glynn(C), C, kind="definition")
+    B = inputs.bernoulli01(10, 10, 8963, 0.6)
+    assert run(capi, "perm_combinatoric", B, dev, small) == oracle.subset_dp(B.astype(np.int64))
+    with pytest.raises(capi.PermError):
+        capi.perm_combinatoric(to_dev(B, dev), opts=dict(block=256))  # int128 partials: 128 threads at most
+
+
 def test_transposed_and_complex(capi, dev):
     A = inputs.uniform_real(7, 4, 8301)
     close(run(capi, "perm_combinatoric", A, dev), oracle.definition(A.T), A, kind="definition")
