@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import U, U_FIX, close, device, read_golden, real_default_kind, run, scale, to_dev
+from gpu_util import U, U_CFIX, U_FIX, close, device, read_golden, real_default_kind, run, scale, to_dev
 from paper_2510_03421_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -209,6 +209,27 @@ def test_rectangle_against_oracle(capi, dev, m, n, arith):
     close(run(capi, "perm_glynn", np.ascontiguousarray(A.T), dev, dict(arith=arith)), ref, A, rel=1e-12, c=2,
           u=U_FIX, kind=kind)
     assert tol <= 2e-9 * abs(ref)
+
+
+@pytest.mark.parametrize("opts", [dict(grid=1, block=32), dict(grid=5, block=64, chunk_log2=2),
+                                  dict(grid=3, block=96, chunk_log2=1), dict(grid=152, block=128, chunk_log2=4)])
+def test_closed_form_launch_shapes(capi, dev, opts):
+    # the closed-form padding sum walks 2^(m-1) sign vectors in aligned chunks, a warp's
+    # lanes on consecutive chunks, the column sums of every thread in shared memory: user
+    # grid, block and chunk sizes (idle lanes, ragged rounds) give the same sum, and the
+    # bound variant's stated error still covers the exact value
+    import torch
+    from oracle import exact
+    A = inputs.uniform_real(11, 17, 7961)
+    assert real_default_kind(A) == "esym"
+    ref = float(exact.glynn_rect_grouped(A))
+    close(run(capi, "perm_glynn", A, dev, opts), ref, A, rel=1e-12, c=2, u=U_FIX, kind="esym")
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = capi.perm_glynn(to_dev(A, dev), opts=dict(opts, err=err))
+    torch.cuda.synchronize(dev)
+    assert abs(capi.value(out, capi.PERM_F64) - ref) <= float(err.item())
+    C = inputs.complex_gaussian(9, 14, 7962)  # truth: the oracle's rectangular Ryser
+    close(run(capi, "perm_glynn", C, dev, opts), oracle.ryser_rect(C), C, rel=1e-12, c=8, u=U_CFIX, kind="esym")
 
 
 @pytest.mark.parametrize("m,n", [(3, 17), (6, 40), (1, 40), (20, 40)])
