@@ -106,6 +106,25 @@ def test_integer_pipes_error_bound_and_grids(capi, dev):
         close(run(capi, "perm_ryser", A, dev, opts), ref, A, kind="ryser", c=2, u=U_FIX)
 
 
+@pytest.mark.parametrize("opts", [dict(grid=1, block=32, chunk_log2=3), dict(grid=11, block=96, chunk_log2=10),
+                                  dict(grid=3, block=64, chunk_log2=16), dict()])
+def test_integer_pipes_rectangle_chunk_orders(capi, dev, opts):
+    # 12 x 20: the subsets of size <= 12 are 87% of the 2^20, so the integer-pipe Gray walk
+    # over all subsets runs (not the by-size walk); with at least 2^6 chunks it hands them
+    # out by the popcount of their high bits (chunk_log2 = 3, 10, planner), with fewer in
+    # Gray order (chunk_log2 = 16).  Against the exact value, with and without a bound.
+    import torch
+    from oracle import exact
+    A = inputs.uniform_real(12, 20, 6811)
+    ref = float(exact.glynn_rect_grouped(A))
+    o = dict(opts, arith=2)
+    close(run(capi, "perm_ryser", A, dev, o), ref, A, kind="ryser", c=2, u=U_FIX)
+    err = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = capi.perm_ryser(to_dev(A, dev), opts=dict(o, err=err))
+    torch.cuda.synchronize(dev)
+    assert abs(capi.value(out, capi.PERM_F64) - ref) <= float(err.item())
+
+
 def test_config_rect20x40_ryser_against_exact_golden(capi, dev):
     # the 20 x 40 uniform[0,1] workload by rectangular Ryser: 2^40 Gray-ordered subsets,
     # the 6.19e11 of size <= 20 weighted by C(40-s, 20-s); the stored truth is exact
